@@ -1,0 +1,437 @@
+#!/usr/bin/env python3
+"""Throughput of Pauli-rotation time evolution on one GB300 (or N replicas).
+
+Workload (the n = 30 qDRIFT configuration): a synthetic Jordan-Wigner-like
+Hamiltonian with 10^4 terms on 30 qubits (one-norm 7.5), qDRIFT with
+N = 10^5 samples at t = 1, applied to a complex64 state that starts as an
+8-determinant superposition.  The run is split into 10 segments of 10^4
+rotations; one benchmark step applies one segment and reads the overlap
+<psi0|psi> (FP64) back to the host, so 10 timed steps are one complete
+qDRIFT run.  Every state is 8 GiB, far larger than the 129 MB L2, so no L2
+flush is needed between steps.
+
+Reported beside the headline (complex64, fused windows): the FP64
+(complex128) path on a 1000-rotation prefix of the same stream and its
+distance to the complex64 result; the CPU oracle on a bounded prefix.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Pauli rotations/sec and HBM GB/s at n=30, complex64 fused vs FP64 at stated error"
+UNIT = "rotations/s"
+N_QUBITS = 30
+N_TERMS = 10_000
+HAM_SEED = 3
+N_SAMPLES = 100_000
+T_TOTAL = 1.0
+QDRIFT_SEED = 4
+PSI0_SEED = 11
+SEGMENTS = 10
+SEG_LEN = N_SAMPLES // SEGMENTS
+FP64_PREFIX = 1000
+CPU_SAMPLE_ROTATIONS = 2
+FALLBACK_HBM_GBS = 6800.0
+WORKLOAD = (f"qdrift n={N_QUBITS} complex64: JW-like H with {N_TERMS} terms (lambda 7.5), "
+            f"N={N_SAMPLES} samples at t={T_TOTAL}, {SEGMENTS} segments of {SEG_LEN} rotations "
+            f"+ FP64 overlap per step, 8-determinant initial state")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=SEGMENTS)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ------------------------------------------------------------ peaks, clocks
+
+def hbm_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            v = float(json.load(f)["hbm_gbs"])
+        return v, "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.proc = None
+        self.gpu = gpu_index
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out = ""
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in out.splitlines():
+            f = [p.strip() for p in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, f[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def kernel_traffic():
+    """Per-launch DRAM bytes of the tile kernel from the committed ncu summary, if the
+    kernel source is unchanged since it was taken."""
+    path = os.path.join(ROOT, "profiles", "k_tile_c64_n30.txt")
+    src = os.path.join(ROOT, "paper_2504_17881_gb300", "csrc", "ps_kernels.cu")
+    try:
+        text = open(path).read()
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    except OSError:
+        return None
+    fields = dict(ln.split(":", 1) for ln in text.splitlines() if ":" in ln and not ln.startswith(" "))
+    if fields.get("kernel_source_sha256", "").strip() != sha:
+        return None
+    try:
+        return float(fields["traffic_bytes_per_launch_full"].strip())
+    except (KeyError, ValueError):
+        return None
+
+
+# --------------------------------------------------------------- workload
+
+def make_workload(rank: int):
+    from paper_2504_17881_gb300 import inputs
+    x, z, h = inputs.jw_hamiltonian(N_QUBITS, N_TERMS, seed=HAM_SEED)
+    idx, amp = inputs.determinant_state(N_QUBITS, seed=PSI0_SEED)
+    return x, z, h, idx, amp, QDRIFT_SEED + rank
+
+
+def cpu_baseline_sample(rotations: int):
+    """Time the oracle (complex128, single thread) on the first `rotations` of the stream."""
+    import oracle
+    from paper_2504_17881_gb300 import inputs
+    x, z, h = inputs.jw_hamiltonian(N_QUBITS, N_TERMS, seed=HAM_SEED)
+    idx = oracle.qdrift_indices(h, QDRIFT_SEED, 0, rotations).astype(np.int64)
+    lam = 0.0
+    for v in h:
+        lam += abs(float(v))
+    tau = lam * T_TOTAL / N_SAMPLES
+    xs, zs = x[idx], z[idx]
+    ph = np.where(h[idx] > 0, tau, -tau)
+    sidx, samp = inputs.determinant_state(N_QUBITS, seed=PSI0_SEED)
+    psi = np.zeros(1 << N_QUBITS, dtype=np.complex128)
+    psi[sidx.astype(np.int64)] = samp
+    tmp = np.zeros_like(psi)
+    t0 = time.perf_counter()
+    oracle.apply_inplace(psi, tmp, xs, zs, ph)
+    dt = time.perf_counter() - t0
+    return rotations / dt, dt
+
+
+# ------------------------------------------------------------------- ours
+
+def run_ours(args):
+    import torch
+    import paper_2504_17881_gb300 as ps
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+
+    x, z, h, idx, amp, seed = make_workload(rank)
+    H = ps.Hamiltonian(N_QUBITS, x, z, h)
+    segs = [H.qdrift_stream(T_TOTAL, N_SAMPLES, seed, first=s * SEG_LEN, count=SEG_LEN) for s in range(SEGMENTS)]
+    plans = [ps.Plan(N_QUBITS, ps.PS_C64, *sg) for sg in segs]
+    rot_per_pass = sum(p.info["rotations"] for p in plans) / sum(p.info["windows"] for p in plans)
+
+    def init_state(t):
+        t.zero_()
+        t[torch.as_tensor(idx.astype(np.int64), device=dev)] = torch.as_tensor(amp, device=dev).to(t.dtype)
+
+    psi0 = ps.StateVector(N_QUBITS, dtype=torch.complex64, device=dev)
+    init_state(psi0.tensor)
+    psi = ps.StateVector(N_QUBITS, dtype=torch.complex64, device=dev)
+    psi.set_tuning(kernel_timing=1)
+
+    def barrier():
+        torch.cuda.synchronize(dev)
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    # warm-up
+    psi.copy_from(psi0)
+    for s in range(args.warmup):
+        psi.apply_plan(plans[s % SEGMENTS])
+        psi.overlap(psi0)
+    psi.copy_from(psi0)
+    torch.cuda.synchronize(dev)
+    ps.ps_reset_stats(psi.handle)
+
+    clocks = ClockSampler(local)
+    barrier()
+    clocks.start()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    overlaps = []
+    for s in range(args.steps):
+        psi.apply_plan(plans[s % SEGMENTS])
+        overlaps.append(psi.overlap(psi0))
+    ev1.record(stream)
+    barrier()
+    clock_info = clocks.stop()
+    elapsed_ms = ev0.elapsed_time(ev1)
+    stats = psi.stats()
+    rotations = args.steps * SEG_LEN
+
+    t_max = elapsed_ms
+    tot_rot = rotations
+    launches = sum(stats["launches"].values())
+    if dist is not None:
+        tt = torch.tensor([elapsed_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max = float(tt.item())
+        tr = torch.tensor([rotations, launches], device=dev, dtype=torch.float64)
+        dist.all_reduce(tr)
+        tot_rot, launches = int(tr[0].item()), int(tr[1].item())
+    value = tot_rot / (t_max / 1e3)
+
+    # roofline of the dominant kernel (fused tile kernel), timed live with events
+    tile_ms = stats["kernel_ms"]["tile"]
+    tile_n = max(stats["launches"]["tile"], 1)
+    bytes_per_launch = 2.0 * 8.0 * (1 << N_QUBITS)
+    achieved = bytes_per_launch / (tile_ms / tile_n / 1e3) / 1e9 if tile_ms > 0 else None
+    peak, peak_kind = hbm_peak()
+    roofline = {"bound": "hbm", "kernel": "k_tile<float,3>", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": (achieved / peak) if achieved else None, "traffic": kernel_traffic(),
+                "peak_source": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
+                else "fallback 6.8 TB/s", "algorithmic_bytes_per_launch": bytes_per_launch,
+                "avg_launch_ms": tile_ms / tile_n}
+    step_gbs = stats["bytes"]["tile"] + stats["bytes"]["pair"] + stats["bytes"]["reduce"]
+    step_gbs = step_gbs / (elapsed_ms / 1e3) / 1e9
+
+    # ------------------------------------------------------------- FP64 path
+    fp64 = None
+    if not args.no_fp64:
+        xs, zs, ph = segs[0][0][:FP64_PREFIX], segs[0][1][:FP64_PREFIX], segs[0][2][:FP64_PREFIX]
+        plan64 = ps.Plan(N_QUBITS, ps.PS_C128, xs, zs, ph)
+        plan32 = ps.Plan(N_QUBITS, ps.PS_C64, xs, zs, ph)
+        p64 = ps.StateVector(N_QUBITS, dtype=torch.complex128, device=dev)
+        p64_0 = ps.StateVector(N_QUBITS, dtype=torch.complex128, device=dev)
+        init_state(p64.tensor)
+        init_state(p64_0.tensor)
+        p64.set_tuning(kernel_timing=1)
+        p64.apply_plan(plan64)  # warm-up on a throwaway state
+        init_state(p64.tensor)
+        torch.cuda.synchronize(dev)
+        ps.ps_reset_stats(p64.handle)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        p64.apply_plan(plan64)
+        g64 = p64.overlap(p64_0)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms64 = e0.elapsed_time(e1)
+        st64 = p64.stats()
+        # complex64 on the same prefix, compared with the FP64 state
+        psi.copy_from(psi0)
+        psi.apply_plan(plan32)
+        g32 = psi.overlap(psi0)
+        diff = torch.linalg.vector_norm(psi.tensor.to(torch.complex128) - p64.tensor).item()
+        ref = torch.linalg.vector_norm(p64.tensor).item()
+        tile64 = st64["kernel_ms"]["tile"] / max(st64["launches"]["tile"], 1)
+        fp64 = {"value": FP64_PREFIX / (ms64 / 1e3), "unit": UNIT, "dtype": "f64", "rotations": FP64_PREFIX,
+                "rot_per_pass": plan64.info["rotations"] / max(plan64.info["windows"], 1),
+                "tile_avg_launch_ms": tile64,
+                "tile_achieved_gbs": 2.0 * 16.0 * (1 << N_QUBITS) / (tile64 / 1e3) / 1e9 if tile64 > 0 else None,
+                "bound": "alu (FP64 pipe)",
+                "c64_vs_fp64": {"state_rel_l2": diff / ref, "overlap_abs": abs(g32 - g64),
+                                "after_rotations": FP64_PREFIX}}
+        del p64, p64_0
+        torch.cuda.empty_cache()
+
+    # ------------------------------------------------------------- end to end
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(ps, torch, dev, segs, idx, amp, args.steps)
+
+    if dist is not None:
+        dist.barrier()
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline_leg()
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": N_QUBITS, "terms": N_TERMS, "samples": N_SAMPLES,
+                   "rotations_per_step": SEG_LEN, "state": "complex64 (FP64 trig, norm and overlap)",
+                   "l2": "inputs larger than L2 (8 GiB state vs 129 MB L2), no flush",
+                   "parallelism": f"replicas x{world} (independent qDRIFT seeds)"},
+        "hbm_gbs": step_gbs, "rot_per_pass": rot_per_pass, "overlap_final": [overlaps[-1].real, overlaps[-1].imag],
+        "roofline": roofline, "fp64": fp64, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+        "clocks": clock_info,
+    }
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def run_e2e(ps, torch, dev, segs, idx, amp, steps):
+    """Same metric through the public API from host buffers: the initial state
+    is uploaded from pinned host memory, each step passes the segment's
+    rotations as host arrays (scheduling and upload inside the library) and
+    reads the overlap back."""
+    nbytes = 8 << N_QUBITS
+    host0 = torch.zeros(1 << N_QUBITS, dtype=torch.complex64).pin_memory()
+    host0[torch.as_tensor(idx.astype(np.int64))] = torch.as_tensor(amp).to(torch.complex64)
+    psi = ps.StateVector(N_QUBITS, dtype=torch.complex64, device=dev)
+    psi0 = ps.StateVector(N_QUBITS, dtype=torch.complex64, device=dev)
+    h2d = 0
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    ps.ps_set_state(psi0.handle, host0.data_ptr())
+    ps.ps_set_state(psi.handle, host0.data_ptr())
+    h2d += 2 * nbytes
+    for s in range(steps):
+        xs, zs, ph = segs[s % SEGMENTS]
+        psi.apply_rotations(xs, zs, ph)
+        h2d += xs.nbytes + zs.nbytes + ph.nbytes
+        psi.overlap(psi0)
+    torch.cuda.synchronize(dev)
+    dt = time.perf_counter() - t0
+    del psi, psi0
+    torch.cuda.empty_cache()
+    return {"value": steps * SEG_LEN / dt, "unit": UNIT, "h2d_bytes_per_step": h2d / steps,
+            "d2h_bytes_per_step": 16, "note": "wall clock; includes 2 x 8 GiB state upload, host scheduling, "
+                                              "per-step rotation upload and overlap readback"}
+
+
+def cpu_baseline_leg():
+    try:
+        rate, dt = cpu_baseline_sample(CPU_SAMPLE_ROTATIONS)
+    except Exception as e:  # noqa: BLE001
+        return {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "error": str(e)}
+    return {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"first {CPU_SAMPLE_ROTATIONS} rotations of the same qDRIFT stream at n={N_QUBITS}, "
+                      f"complex128 scatter-form oracle, 1 thread ({dt:.1f} s)",
+            "host_cores_available": os.cpu_count()}
+
+
+# -------------------------------------------------------------- reference
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    from paper_2504_17881_gb300 import inputs
+    x, z, h = inputs.jw_hamiltonian(N_QUBITS, N_TERMS, seed=HAM_SEED)
+    total = args.warmup + args.steps
+    idx = oracle.qdrift_indices(h, QDRIFT_SEED, 0, total).astype(np.int64)
+    lam = 0.0
+    for v in h:
+        lam += abs(float(v))
+    tau = lam * T_TOTAL / N_SAMPLES
+    sidx, samp = inputs.determinant_state(N_QUBITS, seed=PSI0_SEED)
+    psi = np.zeros(1 << N_QUBITS, dtype=np.complex128)
+    psi[sidx.astype(np.int64)] = samp
+    tmp = np.zeros_like(psi)
+
+    def step(j):
+        oracle.apply_inplace(psi, tmp, [x[idx[j]]], [z[idx[j]]], [tau if h[idx[j]] > 0 else -tau])
+
+    for j in range(args.warmup):
+        step(j)
+    t0 = time.perf_counter()
+    for j in range(args.warmup, total):
+        step(j)
+    dt = time.perf_counter() - t0
+    value = args.steps / dt
+    sample = (f"one rotation per step of the same qDRIFT stream at n={N_QUBITS} (complex128 scatter-form "
+              f"oracle, 1 thread); {args.steps} timed steps after {args.warmup} warm-up")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": N_QUBITS, "terms": N_TERMS, "samples": N_SAMPLES},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

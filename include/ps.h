@@ -1,0 +1,239 @@
+/*
+ * ps.h -- C ABI of libps, a single-GPU (GB300, sm_103a) simulator for
+ * sequences of Pauli rotations exp(i phi P) applied to a full 2^n complex
+ * state vector, the hot path of Miller et al., "phase2: Full-State Vector
+ * Simulation of Quantum Time Evolution at Scale" (arXiv:2504.17881).
+ *
+ * Conventions (all from the paper):
+ *   - State: 2^n complex amplitudes, interleaved (re, im), index k = basis
+ *     state |k>, qubit q (1-based) = bit q-1, least significant first
+ *     (Results, "Software implementation").  PS_C64 stores float pairs
+ *     (8 bytes per amplitude), PS_C128 double pairs (16 bytes; the paper's
+ *     `_Complex double`, Methods, "Mathematical model").
+ *   - Pauli string P = bitmask pair (x, z): bit q of x is set iff factor q+1
+ *     is X or Y, bit q of z iff it is Y or Z (Supplementary Methods,
+ *     "Pauli-string bit representation"; XIY -> (5, 4)).  Then
+ *     P|k> = i^{popc(x&z)} (-1)^{popc(k&z)} |k ^ x>.
+ *   - Rotation (x, z, phi) = exp(i phi P) = cos(phi) I + i sin(phi) P
+ *     (Results, "Software implementation").  Sequences are given in
+ *     application order: element 0 acts first.
+ *
+ * Memory and streams: the caller owns every state buffer (typically a
+ * PyTorch tensor) and the CUDA stream.  The library allocates only its own
+ * small device scratch (plan descriptors, reduction partials), freed by the
+ * matching destroy call.  Every call that does not return a host value is
+ * asynchronous on the state's stream; ps_norm, ps_overlap, ps_get_state and
+ * ps_get_stats synchronise that stream.
+ *
+ * Errors: every int-returning call returns PS_OK or a PS_ERR_* code and
+ * leaves a message for ps_last_error() (per host thread).  A call that
+ * fails argument validation touches no device memory.  Kernels never trap.
+ */
+#ifndef PS_H
+#define PS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    PS_OK = 0,
+    PS_ERR_ARG = 1,         /* invalid argument (null pointer, mask bit >= n, bad size...) */
+    PS_ERR_OOM = 2,         /* host or device allocation of library scratch failed */
+    PS_ERR_CUDA = 3,        /* a CUDA runtime call or kernel launch failed */
+    PS_ERR_TIMEOUT = 4,     /* a bounded device-side wait ran out */
+    PS_ERR_UNSUPPORTED = 5  /* valid request this build does not support */
+};
+
+enum { PS_C64 = 0, PS_C128 = 1 };
+
+/* Kernel kinds reported by ps_get_stats. */
+enum { PS_KERNEL_TILE = 0, PS_KERNEL_PAIR = 1, PS_KERNEL_REDUCE = 2, PS_KERNEL_OTHER = 3, PS_KERNEL_KINDS = 4 };
+
+typedef struct ps_state ps_state; /* opaque: one state vector bound to a stream */
+typedef struct ps_ham ps_ham;     /* opaque: Hamiltonian term list H = sum_l h_l P_l */
+typedef struct ps_plan ps_plan;   /* opaque: a rotation sequence scheduled and resident on the device */
+
+/* Scheduling knobs of the fused path.  Zero in any field selects the default. */
+typedef struct ps_tuning {
+    int tile_bits;     /* B: log2 amplitudes held on chip per fused window tile, 6..14
+                          (default 13 for PS_C64, 12 for PS_C128) */
+    int group_bits;    /* G: log2 amplitudes per thread in the register stage, 1..4 (default 3) */
+    int max_window;    /* most rotations per HBM pass (default 64, at most 256) */
+    int pair_single;   /* 1: a window holding one non-diagonal rotation runs the pair-streaming
+                          kernel instead of the tile kernel; 2: never; 0 = default (1) */
+    int kernel_timing; /* 1: time every launch with CUDA events (read with ps_get_stats) */
+} ps_tuning;
+
+/* Counters of a state handle since creation or the last ps_reset_stats. */
+typedef struct ps_stats {
+    uint64_t launches[PS_KERNEL_KINDS];  /* kernel launches per kind */
+    double kernel_ms[PS_KERNEL_KINDS];   /* summed CUDA-event time per kind (kernel_timing = 1) */
+    double bytes[PS_KERNEL_KINDS];       /* algorithmic HBM bytes per kind (each pass reads and
+                                            writes every amplitude once; a reduction reads its inputs) */
+    uint64_t rotations;                  /* rotations applied */
+    uint64_t passes;                     /* HBM passes (windows) executed */
+} ps_stats;
+
+/* Host-side summary of a schedule (no GPU needed to compute it). */
+typedef struct ps_plan_info {
+    uint64_t rotations;       /* rotations in the sequence */
+    uint64_t windows;         /* HBM passes */
+    uint64_t tile_windows;    /* passes run by the fused tile kernel */
+    uint64_t pair_windows;    /* passes run by the pair-streaming kernel */
+    uint64_t subwindows;      /* register-stage rounds summed over tile windows */
+    uint64_t max_window;      /* longest window (rotations) */
+    int tile_bits;            /* B actually used (min(B, n)) */
+    int group_bits;           /* G actually used */
+} ps_plan_info;
+
+/* ---------------------------------------------------------------- library */
+
+/* Message of the last failing call on this host thread ("" if none). Never NULL. */
+const char *ps_last_error(void);
+
+/* ABI version of this header (increments on any signature change). */
+int ps_abi_version(void);
+
+/* Number of CUDA devices visible, or -1 if the CUDA driver cannot be loaded. Host only. */
+int ps_device_count(void);
+
+/* --------------------------------------------------------------- states */
+
+/* Bind a caller-owned device buffer of 2^n amplitudes (dtype PS_C64 or PS_C128,
+ * 16-byte aligned) and a cudaStream_t (NULL = legacy default stream) to a new
+ * handle.  1 <= n <= 40.  Does not touch the buffer.  The buffer and stream
+ * must outlive the handle. */
+int ps_create(int n, int dtype, void *dev_state, void *stream, ps_state **out);
+
+/* Release library scratch owned by the handle (never the caller's buffer).
+ * Synchronises the handle's stream first.  NULL is ignored. */
+void ps_destroy(ps_state *st);
+
+/* Copy 2^n amplitudes from / to host memory (pinned memory is fastest).
+ * ps_set_state is asynchronous: host_src must stay valid until the stream
+ * reaches the copy.  ps_get_state synchronises. */
+int ps_set_state(ps_state *st, const void *host_src);
+int ps_get_state(ps_state *st, void *host_dst);
+
+/* dst <- src (device to device, on dst's stream); same n and dtype. */
+int ps_copy_state(ps_state *dst, const ps_state *src);
+
+/* Scheduling knobs for later calls on this handle (NULL restores defaults). */
+int ps_set_tuning(ps_state *st, const ps_tuning *tuning);
+
+/* ------------------------------------------------------------- rotations */
+
+/* psi <- exp(i phi[count-1] P[count-1]) ... exp(i phi[0] P[0]) psi.
+ * x, z, phi are host arrays of `count` elements, read before return.  Every
+ * mask must have no bit >= n.  count = 0 is a no-op; x = z = 0 applies the
+ * global phase exp(i phi).  The sequence is scheduled into HBM passes
+ * (windows) on the host -- consecutive rotations whose X masks span a small
+ * space share one pass (Eq. 1, common-suffix grouping, in its single-GPU
+ * form) -- then the passes are launched on the stream.  Asynchronous. */
+int ps_apply_rotations(ps_state *st, const uint64_t *x, const uint64_t *z, const double *phi, size_t count);
+
+/* Schedule a sequence once and keep it on the device: ps_plan_create builds
+ * the windows for states of n qubits and `dtype`, uploads them (synchronously,
+ * current device) and returns the plan; ps_plan_apply launches it on a state
+ * of the same n and dtype (asynchronous, no host work besides the launches).
+ * tuning may be NULL (defaults). */
+int ps_plan_create(int n, int dtype, const uint64_t *x, const uint64_t *z, const double *phi, size_t count,
+                   const ps_tuning *tuning, ps_plan **out);
+int ps_plan_apply(ps_state *st, const ps_plan *plan);
+int ps_plan_get_info(const ps_plan *plan, ps_plan_info *out);
+void ps_plan_destroy(ps_plan *plan);
+
+/* Host only: the summary ps_plan_create would produce, without any GPU. */
+int ps_plan_describe(int n, int dtype, const uint64_t *x, const uint64_t *z, const double *phi, size_t count,
+                     const ps_tuning *tuning, ps_plan_info *out);
+
+/* Host only: export the schedule for inspection.  For each rotation j:
+ * window_of[j] = its window index, and for tile windows its tile-local X and
+ * Z masks (xt[j], zt[j]); for each window w: kind[w] (0 tile, 1 pair),
+ * c[w] = log2 contiguous amplitudes per segment, d[w] = number of basis
+ * vectors and basis[w*16 + i] (i < d[w]) the vectors.  Arrays sized by the
+ * caller: count for the per-rotation ones, max_windows for kind, c and d,
+ * 16*max_windows for basis.  *n_windows receives the window count (PS_ERR_ARG
+ * if it exceeds max_windows). */
+int ps_plan_export(int n, int dtype, const uint64_t *x, const uint64_t *z, const double *phi, size_t count,
+                   const ps_tuning *tuning, size_t max_windows, size_t *n_windows, uint32_t *window_of,
+                   uint32_t *xt, uint32_t *zt, int *kind, int *c, int *d, uint64_t *basis);
+
+/* ------------------------------------------------------------ reductions */
+
+/* *out = <psi|psi> = sum_k |psi[k]|^2, accumulated in FP64 from either dtype
+ * in a fixed order (bitwise reproducible on one device).  Synchronises. */
+int ps_norm(ps_state *st, double *out);
+
+/* out[0] + i out[1] = <psi0|psi> = sum_k conj(psi0[k]) psi[k] in FP64, the
+ * signal g(t) = <psi|exp(i t H)|psi> of Methods, "Data analysis" (Eq. 9)
+ * when psi = exp(itH) psi0.  psi0 and psi need the same n and dtype; the
+ * work runs on psi's stream and synchronises it. */
+int ps_overlap(const ps_state *psi0, ps_state *psi, double out[2]);
+
+/* ----------------------------------------------------------- Hamiltonians */
+
+/* Copy a term list H = sum_l h[l] P_l (Eq. 2, Methods, "Hamiltonian
+ * simulation") with L >= 1 terms on n qubits; masks must have no bit >= n.
+ * Host only. */
+int ps_ham_create(int n, size_t L, const uint64_t *x, const uint64_t *z, const double *h, ps_ham **out);
+void ps_ham_destroy(ps_ham *ham);
+
+/* lambda = sum_l |h_l|, summed in term order in FP64.  Host only. */
+double ps_ham_lambda(const ps_ham *ham);
+
+/* ------------------------------------------------ product-formula streams */
+/* Host only.  These write the rotation sequence that the ps_evolve_* calls
+ * apply, so callers can inspect, split or batch it. */
+
+/* qDRIFT (Campbell 2019, named in Methods, "Hamiltonian simulation"):
+ * draws j = first .. first+count-1 of the N-sample run for `seed`; draw j
+ * takes u_j = (SplitMix64 output j+1 of state seed) >> 11, times 2^-53, and
+ * selects the smallest l with cdf[l] > u_j * lambda (cdf = running FP64 sum
+ * of |h| in term order); it applies exp(i sgn(h_l) (lambda t / N) P_l). */
+int ps_qdrift_stream(const ps_ham *ham, double t, uint64_t N, uint64_t seed, uint64_t first, uint64_t count,
+                     uint64_t *x_out, uint64_t *z_out, double *phi_out);
+
+/* Number of rotations ps_partial_stream writes: r * (L_D + Ns) (Ns counted
+ * only if H_R is non-empty with lambda_R > 0). */
+uint64_t ps_partial_length(const ps_ham *ham, size_t L_D, uint32_t r, uint64_t Ns);
+
+/* Partially randomised product formula, first-order reading of Eq. 5
+ * (Methods, "Hamiltonian simulation"): H_D = the L_D terms of largest |h|
+ * (ties: lower index first), H_R = the rest, both in term order; each of r
+ * steps of delta = t / r applies every H_D term as exp(i delta h_l P_l), then
+ * Ns draws from H_R as exp(i sgn(h) (lambda_R delta / Ns) P), with one
+ * SplitMix64 stream (state seed) running through all steps.  Writes
+ * ps_partial_length(...) rotations. */
+int ps_partial_stream(const ps_ham *ham, size_t L_D, double t, uint32_t r, uint64_t Ns, uint64_t seed,
+                      uint64_t *x_out, uint64_t *z_out, double *phi_out);
+
+/* -------------------------------------------------------- time evolution */
+
+/* First-order Trotter, Eq. 3: (prod_{l=1..L} exp(i (t/r) h_l P_l))^r, term 1
+ * applied first in each step.  r >= 1.  Asynchronous. */
+int ps_evolve_trotter(ps_state *st, const ps_ham *ham, double t, uint32_t r);
+
+/* qDRIFT with N samples and seed (see ps_qdrift_stream).  Asynchronous. */
+int ps_evolve_qdrift(ps_state *st, const ps_ham *ham, double t, uint64_t N, uint64_t seed);
+
+/* Partially randomised formula (see ps_partial_stream).  Asynchronous. */
+int ps_evolve_partial(ps_state *st, const ps_ham *ham, size_t L_D, double t, uint32_t r, uint64_t Ns,
+                      uint64_t seed);
+
+/* ------------------------------------------------------------ statistics */
+
+/* Counters since creation or the last reset; synchronises the stream when
+ * kernel timing is on. */
+int ps_get_stats(ps_state *st, ps_stats *out);
+int ps_reset_stats(ps_state *st);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PS_H */

@@ -111,6 +111,15 @@ def apply(psi, x, z, phi) -> np.ndarray:
     return a
 
 
+def apply_inplace(psi: np.ndarray, tmp: np.ndarray, x, z, phi) -> None:
+    """or_apply on caller-owned complex128 buffers (psi updated in place, tmp scratch)."""
+    if psi.dtype != np.complex128 or tmp.dtype != np.complex128 or not psi.flags.c_contiguous:
+        raise ValueError("psi and tmp must be contiguous complex128 arrays")
+    n = psi.size.bit_length() - 1
+    x, z, phi = _u64(x), _u64(z), _f64(phi)
+    _check(_load().or_apply(n, _p(psi), _p(tmp), _p(x), _p(z), _p(phi), x.size), "apply")
+
+
 def overlap(a, b) -> complex:
     a = np.ascontiguousarray(a, dtype=np.complex128)
     b = np.ascontiguousarray(b, dtype=np.complex128)

@@ -1,0 +1,292 @@
+"""ctypes binding of libps (include/ps.h): argument marshalling only.
+
+Every function keeps the C name and raises ``PsError`` (with
+``ps_last_error()``) when the C call returns a non-zero status.  Device
+memory comes from PyTorch tensors; all state arithmetic runs in libps's CUDA
+kernels.  There is no fallback: if ``libps.so`` is missing the import fails.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libps.so")
+
+PS_OK, PS_ERR_ARG, PS_ERR_OOM, PS_ERR_CUDA, PS_ERR_TIMEOUT, PS_ERR_UNSUPPORTED = range(6)
+PS_C64, PS_C128 = 0, 1
+PS_KERNEL_TILE, PS_KERNEL_PAIR, PS_KERNEL_REDUCE, PS_KERNEL_OTHER = range(4)
+KERNEL_KINDS = ("tile", "pair", "reduce", "other")
+
+
+class PsError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"libps error {code}: {msg}")
+        self.code = code
+
+
+class ps_tuning(ctypes.Structure):
+    _fields_ = [("tile_bits", ctypes.c_int), ("group_bits", ctypes.c_int), ("max_window", ctypes.c_int),
+                ("pair_single", ctypes.c_int), ("kernel_timing", ctypes.c_int)]
+
+
+class ps_stats(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_uint64 * 4), ("kernel_ms", ctypes.c_double * 4),
+                ("bytes", ctypes.c_double * 4), ("rotations", ctypes.c_uint64), ("passes", ctypes.c_uint64)]
+
+
+class ps_plan_info(ctypes.Structure):
+    _fields_ = [("rotations", ctypes.c_uint64), ("windows", ctypes.c_uint64), ("tile_windows", ctypes.c_uint64),
+                ("pair_windows", ctypes.c_uint64), ("subwindows", ctypes.c_uint64), ("max_window", ctypes.c_uint64),
+                ("tile_bits", ctypes.c_int), ("group_bits", ctypes.c_int)]
+
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is not built: run `python -m paper_2504_17881_gb300.build` "
+                      "(or __graft_entry__.build()); there is no non-CUDA fallback")
+lib = ctypes.CDLL(LIB_PATH)
+
+_vp, _i, _u32, _u64, _sz, _d = (ctypes.c_void_p, ctypes.c_int, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_size_t,
+                                ctypes.c_double)
+_pp = ctypes.POINTER(ctypes.c_void_p)
+_SIGS = {
+    "ps_last_error": (ctypes.c_char_p, []),
+    "ps_abi_version": (_i, []),
+    "ps_device_count": (_i, []),
+    "ps_create": (_i, [_i, _i, _vp, _vp, _pp]),
+    "ps_destroy": (None, [_vp]),
+    "ps_set_state": (_i, [_vp, _vp]),
+    "ps_get_state": (_i, [_vp, _vp]),
+    "ps_copy_state": (_i, [_vp, _vp]),
+    "ps_set_tuning": (_i, [_vp, ctypes.POINTER(ps_tuning)]),
+    "ps_apply_rotations": (_i, [_vp, _vp, _vp, _vp, _sz]),
+    "ps_plan_create": (_i, [_i, _i, _vp, _vp, _vp, _sz, ctypes.POINTER(ps_tuning), _pp]),
+    "ps_plan_apply": (_i, [_vp, _vp]),
+    "ps_plan_get_info": (_i, [_vp, ctypes.POINTER(ps_plan_info)]),
+    "ps_plan_destroy": (None, [_vp]),
+    "ps_plan_describe": (_i, [_i, _i, _vp, _vp, _vp, _sz, ctypes.POINTER(ps_tuning), ctypes.POINTER(ps_plan_info)]),
+    "ps_plan_export": (_i, [_i, _i, _vp, _vp, _vp, _sz, ctypes.POINTER(ps_tuning), _sz, ctypes.POINTER(_sz), _vp, _vp,
+                            _vp, _vp, _vp, _vp, _vp]),
+    "ps_norm": (_i, [_vp, ctypes.POINTER(_d)]),
+    "ps_overlap": (_i, [_vp, _vp, _vp]),
+    "ps_ham_create": (_i, [_i, _sz, _vp, _vp, _vp, _pp]),
+    "ps_ham_destroy": (None, [_vp]),
+    "ps_ham_lambda": (_d, [_vp]),
+    "ps_qdrift_stream": (_i, [_vp, _d, _u64, _u64, _u64, _u64, _vp, _vp, _vp]),
+    "ps_partial_length": (_u64, [_vp, _sz, _u32, _u64]),
+    "ps_partial_stream": (_i, [_vp, _sz, _d, _u32, _u64, _u64, _vp, _vp, _vp]),
+    "ps_evolve_trotter": (_i, [_vp, _vp, _d, _u32]),
+    "ps_evolve_qdrift": (_i, [_vp, _vp, _d, _u64, _u64]),
+    "ps_evolve_partial": (_i, [_vp, _vp, _sz, _d, _u32, _u64, _u64]),
+    "ps_get_stats": (_i, [_vp, ctypes.POINTER(ps_stats)]),
+    "ps_reset_stats": (_i, [_vp]),
+}
+for _name, (_res, _args) in _SIGS.items():
+    _fn = getattr(lib, _name)
+    _fn.restype = _res
+    _fn.argtypes = _args
+
+
+def ps_last_error() -> str:
+    return lib.ps_last_error().decode()
+
+
+def _check(rc: int):
+    if rc != PS_OK:
+        raise PsError(rc, ps_last_error())
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _u64a(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.uint64))
+
+
+def _f64a(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+
+
+def _tuning(t) -> ps_tuning | None:
+    if t is None:
+        return None
+    if isinstance(t, ps_tuning):
+        return t
+    return ps_tuning(**{k: int(v) for k, v in dict(t).items()})
+
+
+def ps_abi_version() -> int:
+    return lib.ps_abi_version()
+
+
+def ps_device_count() -> int:
+    return lib.ps_device_count()
+
+
+def ps_create(n: int, dtype: int, dev_ptr: int, stream: int | None) -> int:
+    h = ctypes.c_void_p()
+    _check(lib.ps_create(n, dtype, ctypes.c_void_p(dev_ptr), ctypes.c_void_p(stream or 0), ctypes.byref(h)))
+    return h.value
+
+
+def ps_destroy(h: int):
+    lib.ps_destroy(ctypes.c_void_p(h))
+
+
+def ps_set_state(h: int, host_ptr: int):
+    _check(lib.ps_set_state(ctypes.c_void_p(h), ctypes.c_void_p(host_ptr)))
+
+
+def ps_get_state(h: int, host_ptr: int):
+    _check(lib.ps_get_state(ctypes.c_void_p(h), ctypes.c_void_p(host_ptr)))
+
+
+def ps_copy_state(dst: int, src: int):
+    _check(lib.ps_copy_state(ctypes.c_void_p(dst), ctypes.c_void_p(src)))
+
+
+def ps_set_tuning(h: int, tuning=None):
+    t = _tuning(tuning)
+    _check(lib.ps_set_tuning(ctypes.c_void_p(h), ctypes.byref(t) if t is not None else None))
+
+
+def ps_apply_rotations(h: int, x, z, phi):
+    x, z, phi = _u64a(x), _u64a(z), _f64a(phi)
+    if not (x.size == z.size == phi.size):
+        raise ValueError("x, z and phi must have the same length")
+    _check(lib.ps_apply_rotations(ctypes.c_void_p(h), _ptr(x), _ptr(z), _ptr(phi), x.size))
+
+
+def ps_plan_create(n: int, dtype: int, x, z, phi, tuning=None) -> int:
+    x, z, phi = _u64a(x), _u64a(z), _f64a(phi)
+    t = _tuning(tuning)
+    h = ctypes.c_void_p()
+    _check(lib.ps_plan_create(n, dtype, _ptr(x), _ptr(z), _ptr(phi), x.size,
+                              ctypes.byref(t) if t is not None else None, ctypes.byref(h)))
+    return h.value
+
+
+def ps_plan_apply(h: int, plan: int):
+    _check(lib.ps_plan_apply(ctypes.c_void_p(h), ctypes.c_void_p(plan)))
+
+
+def _info_dict(info: ps_plan_info) -> dict:
+    return {f: getattr(info, f) for f, _ in ps_plan_info._fields_}
+
+
+def ps_plan_get_info(plan: int) -> dict:
+    info = ps_plan_info()
+    _check(lib.ps_plan_get_info(ctypes.c_void_p(plan), ctypes.byref(info)))
+    return _info_dict(info)
+
+
+def ps_plan_destroy(plan: int):
+    lib.ps_plan_destroy(ctypes.c_void_p(plan))
+
+
+def ps_plan_describe(n: int, dtype: int, x, z, phi, tuning=None) -> dict:
+    x, z, phi = _u64a(x), _u64a(z), _f64a(phi)
+    t = _tuning(tuning)
+    info = ps_plan_info()
+    _check(lib.ps_plan_describe(n, dtype, _ptr(x), _ptr(z), _ptr(phi), x.size,
+                                ctypes.byref(t) if t is not None else None, ctypes.byref(info)))
+    return _info_dict(info)
+
+
+def ps_plan_export(n: int, dtype: int, x, z, phi, tuning=None) -> dict:
+    x, z, phi = _u64a(x), _u64a(z), _f64a(phi)
+    t = _tuning(tuning)
+    m = x.size
+    maxw = max(1, m)
+    nw = ctypes.c_size_t()
+    window_of = np.zeros(m, np.uint32)
+    xt = np.zeros(m, np.uint32)
+    zt = np.zeros(m, np.uint32)
+    kind = np.zeros(maxw, np.int32)
+    c = np.zeros(maxw, np.int32)
+    d = np.zeros(maxw, np.int32)
+    basis = np.zeros(16 * maxw, np.uint64)
+    _check(lib.ps_plan_export(n, dtype, _ptr(x), _ptr(z), _ptr(phi), m, ctypes.byref(t) if t is not None else None,
+                              maxw, ctypes.byref(nw), _ptr(window_of), _ptr(xt), _ptr(zt), _ptr(kind), _ptr(c),
+                              _ptr(d), _ptr(basis)))
+    w = nw.value
+    return {"window_of": window_of, "xt": xt, "zt": zt, "kind": kind[:w], "c": c[:w], "d": d[:w],
+            "basis": basis[:16 * w].reshape(w, 16)}
+
+
+def ps_norm(h: int) -> float:
+    out = ctypes.c_double()
+    _check(lib.ps_norm(ctypes.c_void_p(h), ctypes.byref(out)))
+    return out.value
+
+
+def ps_overlap(h0: int, h: int) -> complex:
+    out = (ctypes.c_double * 2)()
+    _check(lib.ps_overlap(ctypes.c_void_p(h0), ctypes.c_void_p(h), out))
+    return complex(out[0], out[1])
+
+
+def ps_ham_create(n: int, x, z, h) -> int:
+    x, z, hh = _u64a(x), _u64a(z), _f64a(h)
+    if not (x.size == z.size == hh.size):
+        raise ValueError("x, z and h must have the same length")
+    out = ctypes.c_void_p()
+    _check(lib.ps_ham_create(n, x.size, _ptr(x), _ptr(z), _ptr(hh), ctypes.byref(out)))
+    return out.value
+
+
+def ps_ham_destroy(ham: int):
+    lib.ps_ham_destroy(ctypes.c_void_p(ham))
+
+
+def ps_ham_lambda(ham: int) -> float:
+    return lib.ps_ham_lambda(ctypes.c_void_p(ham))
+
+
+def ps_qdrift_stream(ham: int, t: float, N: int, seed: int, first: int, count: int):
+    x = np.zeros(count, np.uint64)
+    z = np.zeros(count, np.uint64)
+    phi = np.zeros(count, np.float64)
+    _check(lib.ps_qdrift_stream(ctypes.c_void_p(ham), t, N, seed, first, count, _ptr(x), _ptr(z), _ptr(phi)))
+    return x, z, phi
+
+
+def ps_partial_length(ham: int, L_D: int, r: int, Ns: int) -> int:
+    return int(lib.ps_partial_length(ctypes.c_void_p(ham), L_D, r, Ns))
+
+
+def ps_partial_stream(ham: int, L_D: int, t: float, r: int, Ns: int, seed: int):
+    m = ps_partial_length(ham, L_D, r, Ns)
+    x = np.zeros(max(m, 1), np.uint64)
+    z = np.zeros(max(m, 1), np.uint64)
+    phi = np.zeros(max(m, 1), np.float64)
+    _check(lib.ps_partial_stream(ctypes.c_void_p(ham), L_D, t, r, Ns, seed, _ptr(x), _ptr(z), _ptr(phi)))
+    return x[:m], z[:m], phi[:m]
+
+
+def ps_evolve_trotter(h: int, ham: int, t: float, r: int):
+    _check(lib.ps_evolve_trotter(ctypes.c_void_p(h), ctypes.c_void_p(ham), t, r))
+
+
+def ps_evolve_qdrift(h: int, ham: int, t: float, N: int, seed: int):
+    _check(lib.ps_evolve_qdrift(ctypes.c_void_p(h), ctypes.c_void_p(ham), t, N, seed))
+
+
+def ps_evolve_partial(h: int, ham: int, L_D: int, t: float, r: int, Ns: int, seed: int):
+    _check(lib.ps_evolve_partial(ctypes.c_void_p(h), ctypes.c_void_p(ham), L_D, t, r, Ns, seed))
+
+
+def ps_get_stats(h: int) -> dict:
+    s = ps_stats()
+    _check(lib.ps_get_stats(ctypes.c_void_p(h), ctypes.byref(s)))
+    return {"launches": {k: int(s.launches[i]) for i, k in enumerate(KERNEL_KINDS)},
+            "kernel_ms": {k: float(s.kernel_ms[i]) for i, k in enumerate(KERNEL_KINDS)},
+            "bytes": {k: float(s.bytes[i]) for i, k in enumerate(KERNEL_KINDS)},
+            "rotations": int(s.rotations), "passes": int(s.passes)}
+
+
+def ps_reset_stats(h: int):
+    _check(lib.ps_reset_stats(ctypes.c_void_p(h)))

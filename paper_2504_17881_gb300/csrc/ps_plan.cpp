@@ -1,0 +1,282 @@
+// Host scheduler: splits a rotation sequence into HBM passes ("windows").
+//
+// The paper groups rotations that share the Pauli string Q on the upper
+// (node-index) qubits, so that one pairwise exchange serves the whole group
+// (Eq. 1 and its proof in the Supplementary Methods).  On one GPU the analogue
+// is on-chip residency: a sequence of rotations whose X masks x_1..x_L lie in
+// a subspace V of dimension d (modulo the low c index bits) maps every coset
+//     T(k0) = { k0 ^ v ^ o : v in V, o < 2^c }
+// onto itself, because P_l |k> is proportional to |k ^ x_l>.  Each coset is
+// 2^d contiguous, aligned segments of 2^c amplitudes; it is staged on chip
+// once, all L rotations are applied to it, and it is written back once.  The
+// Z masks only contribute phases: on T(k0) the sign (-1)^{popc(k & z)} splits
+// into a coset-constant (-1)^{popc(k0 & z)} -- the +-phi of Eq. 1 with a
+// diagonal Q -- times a sign that depends on tile coordinates only.
+//
+// The scheduler is greedy and keeps the order of the sequence (randomised
+// draws must not be reordered, Methods, "Data analysis"): a window grows
+// until one more rotation would raise dim V above B - c_min, or it holds
+// max_window rotations.  Inside a window the same construction repeats one
+// level down: consecutive rotations whose tile-local X masks span at most G
+// dimensions form a "sub-window" whose 2^G-amplitude orbits each thread keeps
+// in registers.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <sstream>
+
+#include "ps_internal.h"
+
+namespace ps {
+
+namespace {
+
+int top_bit(uint64_t v) { return 63 - __builtin_clzll(v); }
+
+// Echelon basis over GF(2): every vector has a distinct top bit (its pivot).
+struct Echelon {
+    std::vector<uint64_t> vec;  // insertion order
+    // Reduce v against the basis; `coords` receives the indices used.
+    uint64_t reduce(uint64_t v, uint32_t *coords = nullptr) const {
+        uint32_t used = 0;
+        // process pivots from high to low
+        std::vector<int> order(vec.size());
+        for (size_t i = 0; i < vec.size(); ++i) order[i] = (int)i;
+        std::sort(order.begin(), order.end(), [&](int a, int b) { return top_bit(vec[a]) > top_bit(vec[b]); });
+        for (int i : order) {
+            if ((v >> top_bit(vec[i])) & 1) {
+                v ^= vec[i];
+                used |= 1u << i;
+            }
+        }
+        if (coords) *coords = used;
+        return v;
+    }
+    bool add_if_new(uint64_t v) {
+        uint64_t r = reduce(v);
+        if (r == 0) return false;
+        vec.push_back(r);
+        return true;
+    }
+    size_t rank() const { return vec.size(); }
+};
+
+size_t rank_of_shifted(const uint64_t *x, size_t a, size_t b, int c) {
+    Echelon e;
+    for (size_t j = a; j < b; ++j) {
+        uint64_t v = x[j] >> c;
+        if (v) e.add_if_new(v);
+    }
+    return e.rank();
+}
+
+void fill_coeffs(RotDesc &r, uint64_t x, uint64_t z, double phi) {
+    int y = __builtin_popcountll(x & z) & 3;
+    double s = std::sin(phi);
+    double h = std::sin(0.5 * phi);
+    double cm1 = -2.0 * h * h;
+    if (y >> 1) s = -s;
+    r.s64 = s;
+    r.cm1_64 = cm1;
+    r.s32 = (float)s;
+    r.cm1_32 = (float)cm1;
+    r.x = x;
+    r.z = z;
+    r.yodd = (uint8_t)(y & 1);
+    r.zt = 0;
+    r.smask = 0;
+    r.mu = 0;
+}
+
+// Build the register-stage rounds of one tile window (rotations [a, b) of
+// the plan, tile-local masks already in xt / zt).
+void build_subwindows(Plan &p, WinDesc &w, const std::vector<uint32_t> &xt, const std::vector<uint32_t> &zt,
+                      int B, int G) {
+    size_t a = w.rot_off, b = (size_t)w.rot_off + w.nrot;
+    w.sub_off = (int32_t)p.sub.size();
+    w.nsub = 0;
+    size_t j = a;
+    while (j < b) {
+        Echelon gb;
+        size_t start = j;
+        while (j < b) {
+            uint64_t v = xt[j - a];
+            if (v && gb.reduce(v) != 0) {
+                if ((int)gb.rank() >= G) break;
+                gb.add_if_new(v);
+            }
+            ++j;
+        }
+        // pad with unit vectors at the highest free positions (keeps the
+        // lane-varying low bits of the coset representatives contiguous)
+        std::vector<int> pivs;
+        for (uint64_t v : gb.vec) pivs.push_back(top_bit(v));
+        for (int pos = B - 1; (int)gb.rank() < G && pos >= 0; --pos) {
+            if (std::find(pivs.begin(), pivs.end(), pos) != pivs.end()) continue;
+            gb.vec.push_back(1ull << pos);
+            pivs.push_back(pos);
+        }
+        SubDesc sd;
+        std::memset(&sd, 0, sizeof(sd));
+        for (int i = 0; i < G; ++i) sd.u[i] = (uint32_t)gb.vec[i];
+        std::vector<int> sorted = pivs;
+        std::sort(sorted.begin(), sorted.end());
+        for (int i = 0; i < G; ++i) sd.piv[i] = (int8_t)sorted[i];
+        sd.rot_off = (int32_t)start;
+        sd.nrot = (int32_t)(j - start);
+        // per-rotation group coordinates and sign masks
+        for (size_t r = start; r < j; ++r) {
+            uint32_t coords = 0;
+            uint64_t rem = gb.reduce(xt[r - a], &coords);
+            (void)rem;  // zero by construction
+            RotDesc &rd = p.rot[r];
+            rd.mu = (uint8_t)coords;
+            rd.zt = zt[r - a];
+            uint32_t sm = 0;
+            for (int m = 0; m < (1 << G); ++m) {
+                uint32_t U = 0;
+                for (int i = 0; i < G; ++i)
+                    if ((m >> i) & 1) U ^= sd.u[i];
+                sm |= (uint32_t)(__builtin_popcount(U & rd.zt) & 1) << m;
+            }
+            rd.smask = (uint16_t)sm;
+        }
+        p.sub.push_back(sd);
+        ++w.nsub;
+    }
+}
+
+}  // namespace
+
+Tuning resolve_tuning(const ps_tuning *t, int dtype) {
+    Tuning r;
+    r.B = (t && t->tile_bits) ? t->tile_bits : (dtype == PS_C64 ? 13 : 12);
+    r.G = (t && t->group_bits) ? t->group_bits : 3;
+    r.max_window = (t && t->max_window) ? t->max_window : 64;
+    r.pair_single = (t && t->pair_single) ? t->pair_single : 1;
+    r.kernel_timing = t ? t->kernel_timing : 0;
+    return r;
+}
+
+int build_plan(int n, int dtype, const uint64_t *x, const uint64_t *z, const double *phi, size_t count,
+               const Tuning &tun, Plan &p, std::string *err) {
+    auto fail = [&](const std::string &m) {
+        if (err) *err = m;
+        return PS_ERR_ARG;
+    };
+    if (n < 1 || n > kMaxN) return fail("n must be in [1, 40]");
+    if (dtype != PS_C64 && dtype != PS_C128) return fail("dtype must be PS_C64 or PS_C128");
+    int Bmax = dtype == PS_C64 ? 14 : 13;
+    if (tun.B < 6 || tun.B > Bmax) return fail("tile_bits out of range");
+    if (tun.G < 1 || tun.G > kMaxG) return fail("group_bits must be in [1, 4]");
+    if (tun.max_window < 1 || tun.max_window > kMaxWindow) return fail("max_window must be in [1, 256]");
+    if (tun.pair_single != 1 && tun.pair_single != 2) return fail("pair_single must be 0, 1 or 2");
+    if (count && (!x || !z || !phi)) return fail("null rotation array");
+    for (size_t j = 0; j < count; ++j) {
+        if ((x[j] | z[j]) >> n) {
+            std::ostringstream os;
+            os << "rotation " << j << " has a mask bit >= n=" << n;
+            return fail(os.str());
+        }
+        if (!std::isfinite(phi[j])) {
+            std::ostringstream os;
+            os << "rotation " << j << " has a non-finite angle";
+            return fail(os.str());
+        }
+    }
+    const int B = std::min(tun.B, n);
+    if (n - B > 30) return fail("n - tile_bits must be <= 30");
+    const int G = std::min(tun.G, B);
+    // a segment of at least 128 bytes keeps every DRAM access line-sized
+    const int cmin = std::min(dtype == PS_C64 ? 4 : 3, B);
+    p = Plan();
+    p.n = n;
+    p.dtype = dtype;
+    p.B = B;
+    p.G = G;
+    p.rotations = count;
+    p.rot.resize(count);
+    for (size_t j = 0; j < count; ++j) fill_coeffs(p.rot[j], x[j], z[j], phi[j]);
+
+    std::vector<uint32_t> xt, zt;
+    size_t j = 0;
+    while (j < count) {
+        size_t start = j;
+        if (B == n) {
+            // the whole state is one tile
+            j = std::min(count, start + (size_t)tun.max_window);
+        } else {
+            Echelon hb;
+            while (j < count && j - start < (size_t)tun.max_window) {
+                uint64_t v = x[j] >> cmin;
+                if (v && hb.reduce(v) != 0) {
+                    if ((int)hb.rank() + 1 > B - cmin) break;
+                    hb.add_if_new(v);
+                }
+                ++j;
+            }
+        }
+        WinDesc w;
+        std::memset(&w, 0, sizeof(w));
+        w.rot_off = (int32_t)start;
+        w.nrot = (int32_t)(j - start);
+        bool single_pair = (w.nrot == 1 && x[start] != 0 && tun.pair_single == 1 && n >= 2);
+        if (single_pair) {
+            w.kind = 1;
+            w.c = 0;
+            w.d = 1;
+            w.v[0] = x[start];
+            w.piv[0] = (int8_t)top_bit(x[start]);
+            w.sub_off = (int32_t)p.sub.size();
+            w.nsub = 0;
+            p.win.push_back(w);
+            continue;
+        }
+        // tile window: find c with c = B - rank({x >> c}) (rank does not grow with c)
+        int c = B;
+        if (B < n) {
+            c = B - (int)rank_of_shifted(x, start, j, cmin);
+            for (;;) {
+                int cn = B - (int)rank_of_shifted(x, start, j, c);
+                if (cn == c) break;
+                c = cn;
+            }
+        }
+        Echelon hb;
+        for (size_t r = start; r < j; ++r) {
+            uint64_t v = x[r] >> c;
+            if (v) hb.add_if_new(v);
+        }
+        const int d = (int)hb.rank();
+        if (c + d != B || d > kMaxD) return fail("internal scheduler error (window dimension)");
+        w.kind = 0;
+        w.c = c;
+        w.d = d;
+        std::vector<int> piv(d);
+        for (int i = 0; i < d; ++i) {
+            w.v[i] = hb.vec[i] << c;
+            piv[i] = top_bit(w.v[i]);
+        }
+        std::sort(piv.begin(), piv.end());
+        for (int i = 0; i < d; ++i) w.piv[i] = (int8_t)piv[i];
+        // tile-local masks
+        xt.assign(w.nrot, 0);
+        zt.assign(w.nrot, 0);
+        const uint64_t lowmask = (c >= 64) ? ~0ull : ((1ull << c) - 1);
+        for (size_t r = start; r < j; ++r) {
+            uint32_t coords = 0;
+            uint64_t rem = hb.reduce(x[r] >> c, &coords);
+            if (rem != 0) return fail("internal scheduler error (rotation outside window span)");
+            xt[r - start] = (uint32_t)(((uint64_t)coords << c) | (x[r] & lowmask));
+            uint32_t ztile = (uint32_t)(z[r] & lowmask);
+            for (int i = 0; i < d; ++i)
+                ztile |= (uint32_t)(__builtin_popcountll(w.v[i] & z[r]) & 1) << (c + i);
+            zt[r - start] = ztile;
+        }
+        build_subwindows(p, w, xt, zt, B, G);
+        p.win.push_back(w);
+    }
+    return PS_OK;
+}
+
+}  // namespace ps

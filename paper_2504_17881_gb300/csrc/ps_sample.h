@@ -1,0 +1,30 @@
+// Host-side product-formula streams (see ps_sample.cpp).
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "ps_internal.h"
+
+namespace ps {
+
+struct Stream {
+    std::vector<uint64_t> x, z;
+    std::vector<double> phi;
+    void resize(size_t m) {
+        x.resize(m);
+        z.resize(m);
+        phi.resize(m);
+    }
+    size_t size() const { return phi.size(); }
+};
+
+double ham_lambda(const Ham &H);
+void trotter_stream(const Ham &H, double t, uint32_t r, Stream &out);
+int qdrift_stream(const Ham &H, double t, uint64_t N, uint64_t seed, uint64_t first, uint64_t count, uint64_t *xo,
+                  uint64_t *zo, double *po, std::string *err);
+uint64_t partial_length(const Ham &H, size_t L_D, uint32_t r, uint64_t Ns);
+void partial_stream(const Ham &H, size_t L_D, double t, uint32_t r, uint64_t Ns, uint64_t seed, Stream &out);
+
+}  // namespace ps

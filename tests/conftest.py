@@ -10,6 +10,15 @@ if ROOT not in sys.path:
 
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (GB300, sm_103a)")
+    # libps and the oracle are built in-tree (nvcc cross-compiles without a GPU)
+    import importlib.util
+    spec = importlib.util.spec_from_file_location(
+        "_ps_build", os.path.join(ROOT, "paper_2504_17881_gb300", "build.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    mod.build()
+    import oracle
+    oracle.build()
 
 
 def pytest_collection_modifyitems(config, items):

@@ -1,0 +1,307 @@
+"""GPU parity: libps kernels (through the C ABI) against the CPU oracle.
+
+Tolerances (relative L2 error of amplitudes, relative error of overlaps,
+absolute when |g| < 1e-3):
+  * complex128 path: 1e-12 (both sides are FP64; they differ only in
+    summation order and in the gather vs scatter form of one rotation);
+  * complex64 path: 1e-5 for up to a few hundred rotations.  Each rotation
+    rounds every amplitude a few times at 2^-24 ~ 6e-8 relative, so after m
+    rotations the error grows like sqrt(m) * 1e-7 (3e-6 at m = 1000); longer
+    runs are checked against a bound derived the same way.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_2504_17881_gb300 as ps
+from paper_2504_17881_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+TOL = {ps.PS_C128: 1e-12, ps.PS_C64: 1e-5}
+TDT = {ps.PS_C128: torch.complex128, ps.PS_C64: torch.complex64}
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
+
+
+def rel_scalar(a, b):
+    return abs(a - b) / max(abs(b), 1e-3)
+
+
+def gpu_state(n, dtype, host):
+    st = ps.StateVector(n, dtype=TDT[dtype])
+    st.load(host)
+    return st
+
+
+def run_rotations(n, dtype, psi0, x, z, phi, tuning=None):
+    st = gpu_state(n, dtype, psi0)
+    if tuning:
+        st.set_tuning(**tuning)
+    st.apply_rotations(x, z, phi)
+    out = st.to_numpy().astype(np.complex128)
+    ref0 = gpu_state(n, dtype, psi0)
+    g = st.overlap(ref0)
+    nrm = st.norm2()
+    return out, g, nrm
+
+
+# ------------------------------------------- n = 12, 64 random rotations
+
+TUNINGS = [
+    None,
+    {"tile_bits": 6},
+    {"tile_bits": 8, "group_bits": 1},
+    {"tile_bits": 9, "group_bits": 2, "max_window": 5},
+    {"tile_bits": 10, "group_bits": 4},
+    {"max_window": 1},                      # one rotation per pass: pair kernel
+    {"max_window": 1, "pair_single": 2},    # one rotation per pass: tile kernel
+    {"tile_bits": 12, "max_window": 64},    # the whole state is one tile
+]
+
+
+@pytest.mark.parametrize("dtype", [ps.PS_C128, ps.PS_C64])
+@pytest.mark.parametrize("tuning", TUNINGS)
+def test_random_rotations_n12_all_amplitudes(dtype, tuning):
+    n = 12
+    psi0 = inputs.gaussian_state(n, 0)
+    x, z, phi = inputs.random_rotations(n, 64, seed=1)
+    ref = oracle.apply(psi0, x, z, phi)
+    out, g, nrm = run_rotations(n, dtype, psi0, x, z, phi, tuning)
+    assert rel(out, ref) < TOL[dtype]
+    assert rel_scalar(g, oracle.overlap(psi0, ref)) < TOL[dtype]
+    assert abs(nrm - 1.0) < (1e-13 if dtype == ps.PS_C128 else 1e-5)
+
+
+@pytest.mark.parametrize("dtype", [ps.PS_C128, ps.PS_C64])
+@pytest.mark.parametrize("n", [1, 2, 3, 5, 7, 9, 14, 17])
+def test_small_and_ragged_sizes(dtype, n):
+    psi0 = inputs.gaussian_state(n, n)
+    x, z, phi = inputs.random_rotations(n, 37, seed=100 + n)
+    ref = oracle.apply(psi0, x, z, phi)
+    for tuning in (None, {"tile_bits": 6, "max_window": 3}, {"max_window": 1}):
+        out, _, _ = run_rotations(n, dtype, psi0, x, z, phi, tuning)
+        assert rel(out, ref) < TOL[dtype], (n, tuning)
+
+
+@pytest.mark.parametrize("dtype", [ps.PS_C128, ps.PS_C64])
+def test_edge_rotations(dtype):
+    n = 16
+    psi0 = inputs.gaussian_state(n, 3)
+    top = 1 << (n - 1)
+    x = np.array([0, 1, 1, top, top | 1, 0, (1 << n) - 1, 3, 0, top], np.uint64)
+    z = np.array([0, 0, 1, 0, top, (1 << n) - 1, (1 << n) - 1, 2, 5, top | 1], np.uint64)
+    phi = np.array([0.3, -1.1, 2.0, 0.7, math.pi / 2, -0.2, 1e-9, -math.pi, 0.0, 3.0])
+    ref = oracle.apply(psi0, x, z, phi)
+    for tuning in (None, {"max_window": 1}, {"max_window": 1, "pair_single": 2}, {"tile_bits": 7}):
+        out, _, _ = run_rotations(n, dtype, psi0, x, z, phi, tuning)
+        assert rel(out, ref) < TOL[dtype], tuning
+
+
+@pytest.mark.parametrize("dtype", [ps.PS_C128, ps.PS_C64])
+def test_empty_sequence_is_a_no_op(dtype):
+    n = 10
+    psi0 = inputs.gaussian_state(n, 4)
+    st = gpu_state(n, dtype, psi0)
+    before = st.to_numpy()
+    st.apply_rotations([], [], [])
+    assert np.array_equal(st.to_numpy(), before)
+
+
+def test_invalid_mask_touches_nothing():
+    n = 10
+    psi0 = inputs.gaussian_state(n, 5)
+    st = gpu_state(n, ps.PS_C128, psi0)
+    with pytest.raises(ps.PsError):
+        st.apply_rotations([1, 1 << n], [0, 0], [0.1, 0.2])
+    assert np.array_equal(st.to_numpy(), psi0)
+
+
+@pytest.mark.parametrize("dtype", [ps.PS_C128, ps.PS_C64])
+def test_fused_equals_rotation_by_rotation_bitwise(dtype):
+    """Eq. 1 in single-GPU form: a fused window gives the same bits as one pass per rotation."""
+    n = 20
+    xh, zh, hh = inputs.jw_hamiltonian(n, 500, seed=7)
+    H = ps.Hamiltonian(n, xh, zh, hh)
+    x, z, phi = H.qdrift_stream(1.0, 400, 8)
+    psi0 = inputs.gaussian_state(n, 6)
+    fused, _, _ = run_rotations(n, dtype, psi0, x, z, phi)
+    unfused, _, _ = run_rotations(n, dtype, psi0, x, z, phi, {"max_window": 1})
+    tile_only, _, _ = run_rotations(n, dtype, psi0, x, z, phi, {"max_window": 1, "pair_single": 2})
+    assert np.array_equal(fused, unfused)
+    assert np.array_equal(fused, tile_only)
+
+
+@pytest.mark.parametrize("dtype", [ps.PS_C128, ps.PS_C64])
+def test_plan_apply_equals_apply_rotations(dtype):
+    n = 18
+    x, z, phi = inputs.random_rotations(n, 120, seed=9)
+    psi0 = inputs.gaussian_state(n, 10)
+    a, _, _ = run_rotations(n, dtype, psi0, x, z, phi)
+    st = gpu_state(n, dtype, psi0)
+    plan = ps.Plan(n, dtype, x, z, phi)
+    st.apply_plan(plan)
+    assert np.array_equal(st.to_numpy().astype(np.complex128), a)
+    assert plan.info["rotations"] == 120
+
+
+# --------------------------------------------------- reductions
+
+@pytest.mark.parametrize("dtype", [ps.PS_C128, ps.PS_C64])
+@pytest.mark.parametrize("n", [1, 4, 11, 19, 22])
+def test_overlap_and_norm(dtype, n):
+    a = inputs.gaussian_state(n, 20 + n)
+    b = inputs.gaussian_state(n, 40 + n)
+    if dtype == ps.PS_C64:
+        a = a.astype(np.complex64).astype(np.complex128)
+        b = b.astype(np.complex64).astype(np.complex128)
+    sa, sb = gpu_state(n, dtype, a), gpu_state(n, dtype, b)
+    g = sb.overlap(sa)
+    ref = oracle.overlap(a, b)
+    assert abs(g - ref) < 1e-14 * math.sqrt(1 << n) + 1e-15
+    assert abs(sa.norm2() - oracle.norm2(a)) < 1e-13
+    # bitwise reproducible on one device
+    assert sb.overlap(sa) == g
+
+
+# ---------------------------------------- product formulas vs the oracle
+
+@pytest.mark.parametrize("dtype", [ps.PS_C128, ps.PS_C64])
+def test_trotter_vs_oracle(dtype):
+    n = 12
+    x, z, h = inputs.jw_hamiltonian(n, 150, seed=2)
+    psi0 = inputs.gaussian_state(n, 3)
+    H = ps.Hamiltonian(n, x, z, h)
+    for t, r in ((0.1, 1), (0.8, 3)):
+        st = gpu_state(n, dtype, psi0)
+        st.evolve_trotter(H, t, r)
+        ref = oracle.trotter(psi0, x, z, h, t, r)
+        assert rel(st.to_numpy(), ref) < TOL[dtype] * (1 if dtype == ps.PS_C128 else 3)
+
+
+@pytest.mark.parametrize("dtype", [ps.PS_C128, ps.PS_C64])
+def test_qdrift_vs_oracle(dtype):
+    n = 13
+    x, z, h = inputs.jw_hamiltonian(n, 400, seed=4)
+    psi0 = inputs.gaussian_state(n, 5)
+    H = ps.Hamiltonian(n, x, z, h)
+    st = gpu_state(n, dtype, psi0)
+    st.evolve_qdrift(H, 1.0, 300, 77)
+    ref = oracle.qdrift(psi0, x, z, h, 1.0, 300, 77)
+    assert rel(st.to_numpy(), ref) < TOL[dtype]
+    g = st.overlap(gpu_state(n, dtype, psi0))
+    assert rel_scalar(g, oracle.overlap(psi0, ref)) < TOL[dtype]
+
+
+@pytest.mark.parametrize("dtype", [ps.PS_C128, ps.PS_C64])
+def test_partial_vs_oracle(dtype):
+    n = 12
+    x, z, h = inputs.jw_hamiltonian(n, 300, seed=6)
+    psi0 = inputs.gaussian_state(n, 7)
+    H = ps.Hamiltonian(n, x, z, h)
+    st = gpu_state(n, dtype, psi0)
+    st.evolve_partial(H, 30, 0.6, 2, 40, 13)
+    ref = oracle.partial(psi0, x, z, h, 30, 0.6, 2, 40, 13)
+    assert rel(st.to_numpy(), ref) < TOL[dtype]
+
+
+def test_trotter_exact_for_commuting_terms_on_gpu():
+    n = 14
+    rng = np.random.default_rng(8)
+    z = rng.integers(1, 1 << n, 40).astype(np.uint64)
+    x = np.zeros_like(z)
+    h = rng.normal(size=40)
+    psi0 = inputs.gaussian_state(n, 9)
+    H = ps.Hamiltonian(n, x, z, h)
+    k = np.arange(1 << n, dtype=np.uint64)
+    energy = np.zeros(1 << n)
+    for zl, hl in zip(z, h):
+        par = np.array([bin(int(v)).count("1") & 1 for v in (k & zl)])
+        energy += hl * (1 - 2 * par)
+    exact = np.exp(1j * 0.9 * energy) * psi0
+    for r in (1, 4):
+        st = gpu_state(n, ps.PS_C128, psi0)
+        st.evolve_trotter(H, 0.9, r)
+        assert rel(st.to_numpy(), exact) < 1e-12
+
+
+# ------------------------- full size, launch configuration of the benchmark
+
+N30 = 30
+L30 = 10_000
+
+
+@pytest.fixture(scope="module")
+def ham30():
+    x, z, h = inputs.jw_hamiltonian(N30, L30, seed=3)
+    return x, z, h, ps.Hamiltonian(N30, x, z, h)
+
+
+@pytest.mark.parametrize("dtype", [ps.PS_C64, ps.PS_C128])
+def test_n30_sampled_amplitudes_vs_oracle(ham30, dtype):
+    """First 20 rotations of the n=30 qDRIFT run (10^4 terms, N = 10^5) on the
+    8-determinant state; 48 amplitudes in the support checked one by one."""
+    _, _, _, H = ham30
+    xs, zs, ph = H.qdrift_stream(1.0, 100_000, 4, first=0, count=20)
+    idx, amp = inputs.determinant_state(N30, seed=11)
+    st = ps.StateVector(N30, dtype=TDT[dtype])
+    st.tensor.zero_()
+    st.tensor[torch.as_tensor(idx.astype(np.int64), device="cuda")] = torch.as_tensor(amp, device="cuda").to(
+        st.tensor.dtype)
+    st.apply_rotations(xs, zs, ph)
+    rng = np.random.default_rng(12)
+    ks = []
+    for _ in range(48):
+        k = int(idx[rng.integers(len(idx))])
+        for j in range(len(xs)):
+            if rng.random() < 0.5:
+                k ^= int(xs[j])
+        ks.append(k)
+    ks = np.array(ks, dtype=np.uint64)
+    ref = oracle.amplitudes_sparse(N30, idx, amp, xs, zs, ph, ks)
+    got = st.tensor[torch.as_tensor(ks.astype(np.int64), device="cuda")].cpu().numpy().astype(np.complex128)
+    tol = 1e-12 if dtype == ps.PS_C128 else 1e-5
+    assert np.max(np.abs(got - ref)) / np.max(np.abs(ref)) < tol
+    assert abs(st.norm2() - 1.0) < (1e-12 if dtype == ps.PS_C128 else 1e-5)
+    del st
+    torch.cuda.empty_cache()
+
+
+def test_n30_forward_then_inverse_returns_initial_state(ham30):
+    """P^2 = I makes the reversed sequence with negated angles the exact inverse."""
+    _, _, _, H = ham30
+    xs, zs, ph = H.qdrift_stream(1.0, 100_000, 4, first=0, count=3000)
+    idx, amp = inputs.determinant_state(N30, seed=11)
+    st = ps.StateVector(N30, dtype=torch.complex64)
+    st.tensor.zero_()
+    st.tensor[torch.as_tensor(idx.astype(np.int64), device="cuda")] = torch.as_tensor(amp, device="cuda").to(
+        torch.complex64)
+    st.apply_rotations(xs, zs, ph)
+    mid_norm = st.norm2()
+    st.apply_rotations(xs[::-1].copy(), zs[::-1].copy(), -ph[::-1])
+    back = st.tensor[torch.as_tensor(idx.astype(np.int64), device="cuda")].cpu().numpy()
+    # FP32: 6000 rotations, sqrt(6000) * ~1e-7 ~ 1e-5
+    assert np.max(np.abs(back - amp)) < 5e-5
+    assert abs(mid_norm - 1.0) < 5e-5
+    del st
+    torch.cuda.empty_cache()
+
+
+def test_stats_count_launches_and_bytes():
+    n = 16
+    x, z, phi = inputs.random_rotations(n, 50, seed=13)
+    st = gpu_state(n, ps.PS_C64, inputs.gaussian_state(n, 14))
+    st.set_tuning(kernel_timing=1)
+    ps.ps_reset_stats(st.handle)
+    st.apply_rotations(x, z, phi)
+    info = ps.ps_plan_describe(n, ps.PS_C64, x, z, phi)
+    s = st.stats()
+    assert s["rotations"] == 50 and s["passes"] == info["windows"]
+    assert s["launches"]["tile"] + s["launches"]["pair"] == info["windows"]
+    assert s["kernel_ms"]["tile"] + s["kernel_ms"]["pair"] > 0
+    assert s["bytes"]["tile"] + s["bytes"]["pair"] == 2 * 8 * (1 << n) * info["windows"]

@@ -345,7 +345,7 @@ def test_sparse_amplitudes_vs_dense_products():
 
 def test_trotter_term_order_first_term_acts_first():
     n = 3
-    x, z, h = [0b001, 0b011], [0b010, 0b001], [0.9, -1.3]  # non-commuting pair
+    x, z, h = [0b001, 0b010], [0b100, 0b011], [0.9, -1.3]  # X1 Z3 and Z1 Y2 anticommute
     psi = inputs.gaussian_state(n, 61)
     t = 0.6
     ref = expm_herm(dense_pauli(n, x[1], z[1]), t * h[1]) @ (expm_herm(dense_pauli(n, x[0], z[0]), t * h[0]) @ psi)
