@@ -47,7 +47,10 @@ SEG_LEN = N_SAMPLES // SEGMENTS
 FP64_PREFIX = 1000
 CPU_SAMPLE_ROTATIONS = 2
 FALLBACK_HBM_GBS = 6800.0
-WORKLOAD = (f"qdrift n={N_QUBITS} complex64: JW-like H with {N_TERMS} terms (lambda 7.5), "
+
+
+def workload_name():
+    return (f"qdrift n={N_QUBITS} complex64: JW-like H with {N_TERMS} terms (lambda 7.5), "
             f"N={N_SAMPLES} samples at t={T_TOTAL}, {SEGMENTS} segments of {SEG_LEN} rotations "
             f"+ FP64 overlap per step, 8-determinant initial state")
 
@@ -61,6 +64,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--qubits", type=int, default=30,
+                    help="state size; values other than 30 are for profiling captures only")
     return ap.parse_args()
 
 
@@ -296,7 +301,7 @@ def run_ours(args):
         psi.copy_from(psi0)
         psi.apply_plan(plan32)
         g32 = psi.overlap(psi0)
-        diff = torch.linalg.vector_norm(psi.tensor.to(torch.complex128) - p64.tensor).item()
+        diff = torch.linalg.vector_norm(psi.tensor.to(torch.complex128) * psi.scale() - p64.tensor * p64.scale()).item()
         ref = torch.linalg.vector_norm(p64.tensor).item()
         tile64 = st64["kernel_ms"]["tile"] / max(st64["launches"]["tile"], 1)
         fp64 = {"value": FP64_PREFIX / (ms64 / 1e3), "unit": UNIT, "dtype": "f64", "rotations": FP64_PREFIX,
@@ -329,7 +334,7 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n": N_QUBITS, "terms": N_TERMS, "samples": N_SAMPLES,
+        "config": {"workload": workload_name(), "n": N_QUBITS, "terms": N_TERMS, "samples": N_SAMPLES,
                    "rotations_per_step": SEG_LEN, "state": "complex64 (FP64 trig, norm and overlap)",
                    "l2": "inputs larger than L2 (8 GiB state vs 129 MB L2), no flush",
                    "parallelism": f"replicas x{world} (independent qDRIFT seeds)"},
@@ -419,14 +424,16 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n": N_QUBITS, "terms": N_TERMS, "samples": N_SAMPLES},
+        "config": {"workload": workload_name(), "n": N_QUBITS, "terms": N_TERMS, "samples": N_SAMPLES},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
 
 
 def main():
+    global N_QUBITS
     args = parse()
+    N_QUBITS = args.qubits
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -66,6 +66,8 @@ typedef struct ps_tuning {
     int pair_single;   /* 1: a window holding one non-diagonal rotation runs the pair-streaming
                           kernel instead of the tile kernel; 2: never; 0 = default (1) */
     int kernel_timing; /* 1: time every launch with CUDA events (read with ps_get_stats) */
+    int reg_groups;    /* register groups of 2^G amplitudes per thread: 1, 2 or 4 (default: as many
+                          as fit in 32 complex64 / 16 complex128 amplitudes per thread) */
 } ps_tuning;
 
 /* Counters of a state handle since creation or the last ps_reset_stats. */
@@ -162,6 +164,15 @@ int ps_plan_describe(int n, int dtype, const uint64_t *x, const uint64_t *z, con
 int ps_plan_export(int n, int dtype, const uint64_t *x, const uint64_t *z, const double *phi, size_t count,
                    const ps_tuning *tuning, size_t max_windows, size_t *n_windows, uint32_t *window_of,
                    uint32_t *xt, uint32_t *zt, int *kind, int *c, int *d, uint64_t *basis);
+
+/* Stored scale.  A pass applies the cos(phi) factors of its small-angle
+ * rotations only to the precision the storage type represents; the residual
+ * factor f is tracked in FP64 by the handle, so that the represented state is
+ * f * (stored amplitudes).  f = 1 exactly for PS_C128; for PS_C64,
+ * |f - 1| < 2^-24.  ps_norm and ps_overlap include f; ps_set_state resets it
+ * to 1 and ps_copy_state copies it.  This removes the systematic norm drift
+ * that per-rotation rounding of cos(phi) ~ 1 to FP32 would cause. */
+int ps_get_scale(const ps_state *st, double *out);
 
 /* ------------------------------------------------------------ reductions */
 

@@ -13,7 +13,7 @@ from __future__ import annotations
 from . import _lib
 from ._lib import (PS_C64, PS_C128, PsError, ps_abi_version, ps_apply_rotations, ps_copy_state, ps_create,  # noqa: F401
                    ps_destroy, ps_device_count, ps_evolve_partial, ps_evolve_qdrift, ps_evolve_trotter,
-                   ps_get_state, ps_get_stats, ps_ham_create, ps_ham_destroy, ps_ham_lambda, ps_last_error, ps_norm,
+                   ps_get_scale, ps_get_state, ps_get_stats, ps_ham_create, ps_ham_destroy, ps_ham_lambda, ps_last_error, ps_norm,
                    ps_overlap, ps_partial_length, ps_partial_stream, ps_plan_apply, ps_plan_create, ps_plan_describe,
                    ps_plan_destroy, ps_plan_export, ps_plan_get_info, ps_qdrift_stream, ps_reset_stats,
                    ps_set_state, ps_set_tuning)
@@ -74,10 +74,14 @@ class StateVector:
         self.stream.synchronize()
 
     def to_numpy(self):
+        """Stored amplitudes (the represented state is scale() times these)."""
         torch = _torch()
         dst = torch.empty(self.tensor.numel(), dtype=self.tensor.dtype).pin_memory()
         ps_get_state(self.handle, dst.data_ptr())
         return dst.numpy().copy()
+
+    def scale(self) -> float:
+        return ps_get_scale(self.handle)
 
     def copy_from(self, other: "StateVector"):
         ps_copy_state(self.handle, other.handle)

@@ -29,7 +29,7 @@ class PsError(RuntimeError):
 
 class ps_tuning(ctypes.Structure):
     _fields_ = [("tile_bits", ctypes.c_int), ("group_bits", ctypes.c_int), ("max_window", ctypes.c_int),
-                ("pair_single", ctypes.c_int), ("kernel_timing", ctypes.c_int)]
+                ("pair_single", ctypes.c_int), ("kernel_timing", ctypes.c_int), ("reg_groups", ctypes.c_int)]
 
 
 class ps_stats(ctypes.Structure):
@@ -70,6 +70,7 @@ _SIGS = {
     "ps_plan_export": (_i, [_i, _i, _vp, _vp, _vp, _sz, ctypes.POINTER(ps_tuning), _sz, ctypes.POINTER(_sz), _vp, _vp,
                             _vp, _vp, _vp, _vp, _vp]),
     "ps_norm": (_i, [_vp, ctypes.POINTER(_d)]),
+    "ps_get_scale": (_i, [_vp, ctypes.POINTER(_d)]),
     "ps_overlap": (_i, [_vp, _vp, _vp]),
     "ps_ham_create": (_i, [_i, _sz, _vp, _vp, _vp, _pp]),
     "ps_ham_destroy": (None, [_vp]),
@@ -220,6 +221,12 @@ def ps_plan_export(n: int, dtype: int, x, z, phi, tuning=None) -> dict:
 def ps_norm(h: int) -> float:
     out = ctypes.c_double()
     _check(lib.ps_norm(ctypes.c_void_p(h), ctypes.byref(out)))
+    return out.value
+
+
+def ps_get_scale(h: int) -> float:
+    out = ctypes.c_double()
+    _check(lib.ps_get_scale(ctypes.c_void_p(h), ctypes.byref(out)))
     return out.value
 
 

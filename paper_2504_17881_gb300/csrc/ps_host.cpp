@@ -94,6 +94,11 @@ struct ps_state {
     double *partials = nullptr;
     double *rout = nullptr;
     double *hout = nullptr;
+    // The stored amplitudes equal the evolved state divided by `pending`:
+    // cos(phi) factors of tangent-form rotations are applied per pass only to
+    // the precision the storage type holds, the rest is carried here (FP64)
+    // and folded into later passes and into ps_norm / ps_overlap.
+    double pending = 1.0;
     // statistics
     ps_stats stats{};
     std::vector<TimedLaunch> timed;
@@ -187,8 +192,14 @@ int launch_plan(ps_state *st, const Plan &p, const PlanImage &img, void *dev) {
             if (!ea || !eb) return fail(PS_ERR_CUDA, "cudaEventCreate failed");
             PS_CUDA(cudaEventRecord(ea, st->stream), "cudaEventRecord");
         }
-        int e = (w.kind == 1) ? launch_pair(st->dtype, st->psi, st->n, dv, w, (int)wi, st->stream, st->num_sms)
-                              : launch_tile(st->dtype, p.G, st->psi, st->n, p.B, dv, w, (int)wi, st->stream);
+        // split the window's cos(phi) product into the part the storage type
+        // represents (applied by the kernel) and the residual (carried)
+        st->pending *= w.kprod;
+        const double scale = st->dtype == PS_C64 ? (double)(float)st->pending : st->pending;
+        st->pending /= scale;
+        int e = (w.kind == 1)
+                    ? launch_pair(st->dtype, st->psi, st->n, dv, w, (int)wi, scale, st->stream, st->num_sms)
+                    : launch_tile(st->dtype, p.G, p.NG, st->psi, st->n, p.B, dv, w, (int)wi, scale, st->stream);
         if (e != 0) return cuda_fail((cudaError_t)e, w.kind == 1 ? "pair kernel launch" : "tile kernel launch");
         if (timing) {
             PS_CUDA(cudaEventRecord(eb, st->stream), "cudaEventRecord");
@@ -353,6 +364,7 @@ int ps_set_state(ps_state *st, const void *host_src) {
     if (!host_src) return fail(PS_ERR_ARG, "null host buffer");
     DeviceGuard g(st->device);
     PS_CUDA(cudaMemcpyAsync(st->psi, host_src, state_bytes(st), cudaMemcpyHostToDevice, st->stream), "ps_set_state");
+    st->pending = 1.0;
     return PS_OK;
 }
 
@@ -372,6 +384,7 @@ int ps_copy_state(ps_state *dst, const ps_state *src) {
     DeviceGuard g(dst->device);
     PS_CUDA(cudaMemcpyAsync(dst->psi, src->psi, state_bytes(dst), cudaMemcpyDeviceToDevice, dst->stream),
             "ps_copy_state");
+    dst->pending = src->pending;
     return PS_OK;
 }
 
@@ -521,7 +534,7 @@ int ps_norm(ps_state *st, double *out) {
     double r[2];
     int rc = reduce(st, 0, st->psi, nullptr, r);
     if (rc) return rc;
-    *out = r[0];
+    *out = r[0] * st->pending * st->pending;
     return PS_OK;
 }
 
@@ -538,7 +551,19 @@ int ps_overlap(const ps_state *psi0, ps_state *psi, double out[2]) {
         cudaStreamWaitEvent(psi->stream, e, 0);
         cudaEventDestroy(e);
     }
-    return reduce(psi, 1, psi0->psi, psi->psi, out);
+    int rc = reduce(psi, 1, psi0->psi, psi->psi, out);
+    if (rc) return rc;
+    const double f = psi0->pending * psi->pending;
+    out[0] *= f;
+    out[1] *= f;
+    return PS_OK;
+}
+
+int ps_get_scale(const ps_state *st, double *out) {
+    if (int rc = check_state(st)) return rc;
+    if (!out) return fail(PS_ERR_ARG, "null output pointer");
+    *out = st->pending;
+    return PS_OK;
 }
 
 int ps_ham_create(int n, size_t L, const uint64_t *x, const uint64_t *z, const double *h, ps_ham **out) {

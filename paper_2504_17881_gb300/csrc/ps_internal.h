@@ -15,21 +15,24 @@ constexpr int kMaxG = 4;        // most group bits in the register stage
 constexpr int kMaxWindow = 256; // most rotations per window
 constexpr int kMaxN = 40;
 
-// One rotation as the kernels consume it.  `s` carries sin(phi) times
-// (-1)^{floor(y/2)} with y = popc(x & z) mod 4, so that the update of
-// amplitude j reads (gather form of cos(phi) I + i sin(phi) P):
-//   a'[j] = a[j] + cm1 a[j] + s (-1)^{popc(j & z)} rotY(a[j ^ x]),
-//   rotY(b) = (-b.im, b.re) for even y, (b.re, b.im) for odd y,
-// where cm1 = cos(phi) - 1 = -2 sin^2(phi/2) (no cancellation for small phi).
+// One rotation as the kernels consume it.  With y = popc(x & z) mod 4 the
+// gather form of exp(i phi P) = cos(phi) I + i sin(phi) P on amplitude j is
+//   a'[j] = cos(phi) a[j] + sin(phi) (-1)^{floor(y/2)} (-1)^{popc(j & z)} rotY(a[j ^ x]),
+//   rotY(b) = (-b.im, b.re) for even y, (b.re, b.im) for odd y.
+// Tangent form (|tan phi| <= 1): a'[j] = cos(phi) (a[j] + base (-1)^{popc(j&z)} rotY(a[j^x]))
+// with base = tan(phi) (-1)^{floor(y/2)}; the cos(phi) factors of a window are
+// multiplied together and applied once per pass (two fused multiply-adds per
+// amplitude and rotation instead of four).  Full form (|tan phi| > 1): base =
+// sin(phi) (-1)^{floor(y/2)} and the cos(phi) a[j] term is kept explicitly.
 struct RotDesc {
-    double s64, cm1_64;  // FP64 coefficients (PS_C128)
-    float s32, cm1_32;   // the same, rounded once to FP32 (PS_C64)
-    uint64_t z;          // global Z mask (tile sign)
+    double base64, c64;  // FP64 coefficients (PS_C128); c64 = cos(phi) for the full form
+    float base32, c32;   // the same, rounded once to FP32 (PS_C64)
+    uint64_t z;          // global Z mask (coset sign)
     uint64_t x;          // global X mask (pair kernel)
     uint32_t zt;         // Z mask in tile coordinates
     uint16_t smask;      // bit m: parity(U(m) & zt), U(m) = combination m of the group basis
     uint8_t mu;          // X mask in group coordinates
-    uint8_t yodd;        // popc(x & z) & 1
+    uint8_t flags;       // bit 0: popc(x & z) & 1; bit 1: full form
 };
 
 // A register-stage round inside a tile window: every thread owns groups of
@@ -54,6 +57,7 @@ struct WinDesc {
     int32_t rot_off, nrot;
     int32_t sub_off, nsub;
     int32_t pad;
+    double kprod;         // product of cos(phi) over the window's tangent-form rotations
 };
 
 struct Plan {
@@ -61,6 +65,7 @@ struct Plan {
     int dtype = 0;
     int B = 0;  // tile bits used
     int G = 0;  // group bits used
+    int NG = 0; // register groups per thread requested (0 = automatic)
     std::vector<WinDesc> win;
     std::vector<SubDesc> sub;
     std::vector<RotDesc> rot;
@@ -68,7 +73,7 @@ struct Plan {
 };
 
 struct Tuning {
-    int B, G, max_window, pair_single, kernel_timing;
+    int B, G, max_window, pair_single, kernel_timing, reg_groups;
 };
 
 Tuning resolve_tuning(const ps_tuning *t, int dtype);
@@ -92,10 +97,12 @@ struct DevPlanView {
     const SubDesc *sub;
     const RotDesc *rot;
 };
-int launch_tile(int dtype, int G, void *psi, int n, int B, const DevPlanView &dp, const WinDesc &hw, int wi,
-                void *stream);
-int launch_pair(int dtype, void *psi, int n, const DevPlanView &dp, const WinDesc &hw, int wi, void *stream,
-                int num_sms);
+// `scale` multiplies every amplitude of the pass after its rotations (the
+// part of the accumulated cos(phi) factors the state stores).
+int launch_tile(int dtype, int G, int ng_request, void *psi, int n, int B, const DevPlanView &dp, const WinDesc &hw,
+                int wi, double scale, void *stream);
+int launch_pair(int dtype, void *psi, int n, const DevPlanView &dp, const WinDesc &hw, int wi, double scale,
+                void *stream, int num_sms);
 int launch_reduce(int dtype, int what, const void *a, const void *b, int n, double *partials, double *out_dev,
                   void *stream);
 int reduce_blocks();

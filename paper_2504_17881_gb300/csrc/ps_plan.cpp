@@ -71,22 +71,25 @@ size_t rank_of_shifted(const uint64_t *x, size_t a, size_t b, int c) {
 }
 
 void fill_coeffs(RotDesc &r, uint64_t x, uint64_t z, double phi) {
-    int y = __builtin_popcountll(x & z) & 3;
-    double s = std::sin(phi);
-    double h = std::sin(0.5 * phi);
-    double cm1 = -2.0 * h * h;
-    if (y >> 1) s = -s;
-    r.s64 = s;
-    r.cm1_64 = cm1;
-    r.s32 = (float)s;
-    r.cm1_32 = (float)cm1;
+    const int y = __builtin_popcountll(x & z) & 3;
+    const double sn = std::sin(phi), cs = std::cos(phi);
+    const bool full = std::fabs(sn) > std::fabs(cs);
+    double base = full ? sn : sn / cs;
+    if (y >> 1) base = -base;
+    r.base64 = base;
+    r.c64 = full ? cs : 1.0;
+    r.base32 = (float)base;
+    r.c32 = (float)r.c64;
     r.x = x;
     r.z = z;
-    r.yodd = (uint8_t)(y & 1);
+    r.flags = (uint8_t)((y & 1) | (full ? 2 : 0));
     r.zt = 0;
     r.smask = 0;
     r.mu = 0;
 }
+
+// cos(phi) of a tangent-form rotation (1 for the full form).
+double tangent_scale(const RotDesc &r, double phi) { return (r.flags & 2) ? 1.0 : std::cos(phi); }
 
 // Build the register-stage rounds of one tile window (rotations [a, b) of
 // the plan, tile-local masks already in xt / zt).
@@ -155,6 +158,7 @@ Tuning resolve_tuning(const ps_tuning *t, int dtype) {
     r.max_window = (t && t->max_window) ? t->max_window : 64;
     r.pair_single = (t && t->pair_single) ? t->pair_single : 1;
     r.kernel_timing = t ? t->kernel_timing : 0;
+    r.reg_groups = t ? t->reg_groups : 0;
     return r;
 }
 
@@ -171,6 +175,8 @@ int build_plan(int n, int dtype, const uint64_t *x, const uint64_t *z, const dou
     if (tun.G < 1 || tun.G > kMaxG) return fail("group_bits must be in [1, 4]");
     if (tun.max_window < 1 || tun.max_window > kMaxWindow) return fail("max_window must be in [1, 256]");
     if (tun.pair_single != 1 && tun.pair_single != 2) return fail("pair_single must be 0, 1 or 2");
+    if (tun.reg_groups != 0 && tun.reg_groups != 1 && tun.reg_groups != 2 && tun.reg_groups != 4)
+        return fail("reg_groups must be 0, 1, 2 or 4");
     if (count && (!x || !z || !phi)) return fail("null rotation array");
     for (size_t j = 0; j < count; ++j) {
         if ((x[j] | z[j]) >> n) {
@@ -194,6 +200,7 @@ int build_plan(int n, int dtype, const uint64_t *x, const uint64_t *z, const dou
     p.dtype = dtype;
     p.B = B;
     p.G = G;
+    p.NG = tun.reg_groups;
     p.rotations = count;
     p.rot.resize(count);
     for (size_t j = 0; j < count; ++j) fill_coeffs(p.rot[j], x[j], z[j], phi[j]);
@@ -220,6 +227,8 @@ int build_plan(int n, int dtype, const uint64_t *x, const uint64_t *z, const dou
         std::memset(&w, 0, sizeof(w));
         w.rot_off = (int32_t)start;
         w.nrot = (int32_t)(j - start);
+        w.kprod = 1.0;
+        for (size_t r = start; r < j; ++r) w.kprod *= tangent_scale(p.rot[r], phi[r]);
         bool single_pair = (w.nrot == 1 && x[start] != 0 && tun.pair_single == 1 && n >= 2);
         if (single_pair) {
             w.kind = 1;
