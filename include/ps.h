@@ -59,15 +59,16 @@ typedef struct ps_plan ps_plan;   /* opaque: a rotation sequence scheduled and r
 
 /* Scheduling knobs of the fused path.  Zero in any field selects the default. */
 typedef struct ps_tuning {
-    int tile_bits;     /* B: log2 amplitudes held on chip per fused window tile, 6..14
-                          (default 13 for PS_C64, 12 for PS_C128) */
-    int group_bits;    /* G: log2 amplitudes per thread in the register stage, 1..4 (default 3) */
+    int tile_bits;     /* B: log2 amplitudes per fused window tile, 6..13 for PS_C64,
+                          6..12 for PS_C128 (default 13 / 12) */
+    int group_bits;    /* G: log2 amplitudes per register group, 1..5 for PS_C64, 1..4 for
+                          PS_C128 (default 3) */
     int max_window;    /* most rotations per HBM pass (default 64, at most 256) */
     int pair_single;   /* 1: a window holding one non-diagonal rotation runs the pair-streaming
                           kernel instead of the tile kernel; 2: never; 0 = default (1) */
     int kernel_timing; /* 1: time every launch with CUDA events (read with ps_get_stats) */
-    int reg_groups;    /* register groups of 2^G amplitudes per thread: 1, 2 or 4 (default: as many
-                          as fit in 32 complex64 / 16 complex128 amplitudes per thread) */
+    int reg_groups;    /* register groups of 2^G amplitudes per thread: 1, 2 or 4 (default 4 for
+                          PS_C64, 2 for PS_C128; capped at 32 / 16 amplitudes per thread) */
 } ps_tuning;
 
 /* Counters of a state handle since creation or the last ps_reset_stats. */
@@ -168,8 +169,9 @@ int ps_plan_export(int n, int dtype, const uint64_t *x, const uint64_t *z, const
 /* Stored scale.  A pass applies the cos(phi) factors of its small-angle
  * rotations only to the precision the storage type represents; the residual
  * factor f is tracked in FP64 by the handle, so that the represented state is
- * f * (stored amplitudes).  f = 1 exactly for PS_C128; for PS_C64,
- * |f - 1| < 2^-24.  ps_norm and ps_overlap include f; ps_set_state resets it
+ * f * (stored amplitudes).  f = 1 up to FP64 rounding for PS_C128; for
+ * PS_C64, |f - 1| <= 2^-16 (the factor is applied once it exceeds that, as
+ * a <- a + (f - 1) a, so that its rounding is unbiased).  ps_norm and ps_overlap include f; ps_set_state resets it
  * to 1 and ps_copy_state copies it.  This removes the systematic norm drift
  * that per-rotation rounding of cos(phi) ~ 1 to FP32 would cause. */
 int ps_get_scale(const ps_state *st, double *out);

@@ -36,33 +36,52 @@ static int cuda_fail(cudaError_t e, const char *what) {
         if (e__ != cudaSuccess) return cuda_fail(e__, what); \
     } while (0)
 
-static size_t align16(size_t v) { return (v + 15) & ~(size_t)15; }
-
-// Packed device image of a plan: [WinDesc...][SubDesc...][RotDesc...].
-struct PlanImage {
-    std::vector<unsigned char> bytes;
-    size_t off_sub = 0, off_rot = 0;
-};
-
-static void pack_plan(const Plan &p, PlanImage &img) {
-    const size_t wbytes = align16(p.win.size() * sizeof(WinDesc));
-    const size_t sbytes = align16(p.sub.size() * sizeof(SubDesc));
-    const size_t rbytes = align16(p.rot.size() * sizeof(RotDesc));
-    img.off_sub = wbytes;
-    img.off_rot = wbytes + sbytes;
-    img.bytes.assign(wbytes + sbytes + rbytes + 16, 0);
-    if (!p.win.empty()) std::memcpy(img.bytes.data(), p.win.data(), p.win.size() * sizeof(WinDesc));
-    if (!p.sub.empty()) std::memcpy(img.bytes.data() + img.off_sub, p.sub.data(), p.sub.size() * sizeof(SubDesc));
-    if (!p.rot.empty()) std::memcpy(img.bytes.data() + img.off_rot, p.rot.data(), p.rot.size() * sizeof(RotDesc));
+// Kernel parameters of one window, read from the host copy of the plan.
+static void fill_tile_params(const Plan &p, const WinDesc &w, TileParams &tp) {
+    std::memset(&tp, 0, sizeof(tp));
+    for (int i = 0; i < w.d; ++i) {
+        tp.v[i] = w.v[i];
+        tp.piv[i] = w.piv[i];
+    }
+    tp.c = w.c;
+    tp.d = w.d;
+    tp.nsub = w.nsub;
+    tp.nrot = w.nrot;
+    for (int s = 0; s < w.nsub; ++s) {
+        const SubDesc &sd = p.sub[w.sub_off + s];
+        for (int i = 0; i < kMaxG; ++i) {
+            tp.sub[s].u[i] = sd.u[i];
+            tp.sub[s].piv[i] = sd.piv[i];
+        }
+        tp.sub[s].r0 = (uint8_t)(sd.rot_off - w.rot_off);
+        tp.sub[s].r1 = (uint8_t)(sd.rot_off - w.rot_off + sd.nrot);
+        bool fast = sd.nrot >= 1 && sd.nrot <= p.G;
+        for (int r = 0; r < sd.nrot && fast; ++r) {
+            const RotDesc &rd = p.rot[sd.rot_off + r];
+            fast = rd.mu == (1u << r) && rd.flags == 0;
+        }
+        tp.sub[s].fast = fast ? (uint8_t)sd.nrot : 0;
+    }
+    for (int r = 0; r < w.nrot; ++r) {
+        const RotDesc &rd = p.rot[w.rot_off + r];
+        TileRotP &rp = tp.rot[r];
+        rp.base = rd.base64;
+        rp.c = rd.c64;
+        rp.z = rd.z;
+        rp.zt = rd.zt;
+        rp.smask = rd.smask;
+        rp.meta = (uint32_t)rd.mu | ((uint32_t)(rd.flags & 1) << 5) | ((uint32_t)((rd.flags >> 1) & 1) << 6);
+    }
 }
 
-static DevPlanView view_of(void *dev, const PlanImage &img) {
-    DevPlanView v;
-    unsigned char *b = (unsigned char *)dev;
-    v.win = (const WinDesc *)b;
-    v.sub = (const SubDesc *)(b + img.off_sub);
-    v.rot = (const RotDesc *)(b + img.off_rot);
-    return v;
+static void fill_pair_params(const Plan &p, const WinDesc &w, PairParams &pp) {
+    const RotDesc &rd = p.rot[w.rot_off];
+    pp.x = rd.x;
+    pp.z = rd.z;
+    pp.base = rd.base64;
+    pp.c = rd.c64;
+    pp.flags = rd.flags;
+    pp.pad = 0;
 }
 
 struct TimedLaunch {
@@ -82,14 +101,6 @@ struct ps_state {
     int device = 0;
     int num_sms = 0;
     Tuning tun{};
-    // per-state device buffer for plans built by ps_apply_rotations / ps_evolve_*
-    void *dplan = nullptr;
-    size_t dplan_cap = 0;
-    // pinned staging for the plan upload, reusable once `stage_done` has fired
-    void *hstage = nullptr;
-    size_t hstage_cap = 0;
-    cudaEvent_t stage_done = nullptr;
-    bool stage_pending = false;
     // reductions
     double *partials = nullptr;
     double *rout = nullptr;
@@ -110,10 +121,7 @@ struct ps_ham {
 };
 
 struct ps_plan {
-    Plan plan;
-    PlanImage img;
-    void *dev = nullptr;
-    int device = 0;
+    Plan plan;  // host copy; every launch passes its window by value
 };
 
 namespace {
@@ -165,23 +173,21 @@ int ensure_prepared(ps_state *st) {
     std::lock_guard<std::mutex> lock(mu);
     const int slot = 2 * (st->device & 63) + st->dtype;
     if (done[slot]) return PS_OK;
-    const int Bmax = st->dtype == PS_C64 ? 14 : 13;
-    for (int G = 1; G <= kMaxG; ++G) {
-        int e = prepare_kernels(st->dtype, G, Bmax);
-        if (e != 0) return cuda_fail((cudaError_t)e, "cudaFuncSetAttribute (tile kernel shared memory)");
-    }
+    int e = prepare_kernels(st->dtype);
+    if (e != 0) return cuda_fail((cudaError_t)e, "cudaFuncSetAttribute (tile kernel shared memory)");
     done[slot] = 1;
     return PS_OK;
 }
 
-// Launch every window of a plan resident at `dev` on the state's stream.
-int launch_plan(ps_state *st, const Plan &p, const PlanImage &img, void *dev) {
+// Launch every window of a plan on the state's stream.
+int launch_plan(ps_state *st, const Plan &p) {
     if (p.win.empty()) return PS_OK;
     int rc = ensure_prepared(st);
     if (rc) return rc;
-    const DevPlanView dv = view_of(dev, img);
     const bool timing = st->tun.kernel_timing != 0;
     const double pass_bytes = 2.0 * (double)state_bytes(st);
+    TileParams tp;
+    PairParams pp;
     for (size_t wi = 0; wi < p.win.size(); ++wi) {
         const WinDesc &w = p.win[wi];
         const int kind = w.kind == 1 ? PS_KERNEL_PAIR : PS_KERNEL_TILE;
@@ -192,14 +198,27 @@ int launch_plan(ps_state *st, const Plan &p, const PlanImage &img, void *dev) {
             if (!ea || !eb) return fail(PS_ERR_CUDA, "cudaEventCreate failed");
             PS_CUDA(cudaEventRecord(ea, st->stream), "cudaEventRecord");
         }
-        // split the window's cos(phi) product into the part the storage type
-        // represents (applied by the kernel) and the residual (carried)
+        // Carry the window's cos(phi) product; apply it as a <- a + kdelta a
+        // (one rounding, unbiased) once it is far enough from 1 for the
+        // storage type -- always for complex128, beyond 2^-16 for complex64,
+        // where a factor within an ulp of 1 would round away systematically.
         st->pending *= w.kprod;
-        const double scale = st->dtype == PS_C64 ? (double)(float)st->pending : st->pending;
-        st->pending /= scale;
-        int e = (w.kind == 1)
-                    ? launch_pair(st->dtype, st->psi, st->n, dv, w, (int)wi, scale, st->stream, st->num_sms)
-                    : launch_tile(st->dtype, p.G, p.NG, st->psi, st->n, p.B, dv, w, (int)wi, scale, st->stream);
+        double kdelta = 0.0;
+        const double dev = st->pending - 1.0;
+        if (st->dtype == PS_C128) {
+            kdelta = dev;
+        } else if (std::fabs(dev) > 0x1.0p-16) {
+            kdelta = (double)(float)dev;
+        }
+        if (kdelta != 0.0) st->pending /= (1.0 + kdelta);
+        int e;
+        if (w.kind == 1) {
+            fill_pair_params(p, w, pp);
+            e = launch_pair(st->dtype, st->psi, st->n, pp, kdelta, st->stream, st->num_sms);
+        } else {
+            fill_tile_params(p, w, tp);
+            e = launch_tile(st->dtype, p.G, p.NG, st->psi, st->n, tp, kdelta, st->stream);
+        }
         if (e != 0) return cuda_fail((cudaError_t)e, w.kind == 1 ? "pair kernel launch" : "tile kernel launch");
         if (timing) {
             PS_CUDA(cudaEventRecord(eb, st->stream), "cudaEventRecord");
@@ -214,48 +233,14 @@ int launch_plan(ps_state *st, const Plan &p, const PlanImage &img, void *dev) {
     return PS_OK;
 }
 
-// Build, upload (through pinned staging, stream-ordered) and launch.
+// Schedule on the host and launch.
 int run_sequence(ps_state *st, const uint64_t *x, const uint64_t *z, const double *phi, size_t count) {
     if (count == 0) return PS_OK;
     Plan p;
     std::string err;
     int rc = build_plan(st->n, st->dtype, x, z, phi, count, st->tun, p, &err);
     if (rc) return fail(rc, err);
-    PlanImage img;
-    pack_plan(p, img);
-    const size_t need = img.bytes.size();
-    // pinned staging: wait until the previous upload has left it
-    if (st->stage_pending) {
-        PS_CUDA(cudaEventSynchronize(st->stage_done), "cudaEventSynchronize");
-        st->stage_pending = false;
-    }
-    if (st->hstage_cap < need) {
-        if (st->hstage) cudaFreeHost(st->hstage);
-        st->hstage = nullptr;
-        size_t cap = std::max(need, st->hstage_cap * 2);
-        if (cudaMallocHost(&st->hstage, cap) != cudaSuccess) {
-            st->hstage_cap = 0;
-            return fail(PS_ERR_OOM, "cudaMallocHost (plan staging) failed");
-        }
-        st->hstage_cap = cap;
-    }
-    if (st->dplan_cap < need) {
-        // the old buffer may still be read by queued kernels of this stream
-        PS_CUDA(cudaStreamSynchronize(st->stream), "cudaStreamSynchronize");
-        if (st->dplan) cudaFree(st->dplan);
-        st->dplan = nullptr;
-        size_t cap = std::max(need, st->dplan_cap * 2);
-        if (cudaMalloc(&st->dplan, cap) != cudaSuccess) {
-            st->dplan_cap = 0;
-            return fail(PS_ERR_OOM, "cudaMalloc (plan buffer) failed");
-        }
-        st->dplan_cap = cap;
-    }
-    std::memcpy(st->hstage, img.bytes.data(), need);
-    PS_CUDA(cudaMemcpyAsync(st->dplan, st->hstage, need, cudaMemcpyHostToDevice, st->stream), "plan upload");
-    PS_CUDA(cudaEventRecord(st->stage_done, st->stream), "cudaEventRecord");
-    st->stage_pending = true;
-    return launch_plan(st, p, img, st->dplan);
+    return launch_plan(st, p);
 }
 
 int check_state(const ps_state *st) {
@@ -328,7 +313,6 @@ int ps_create(int n, int dtype, void *dev_state, void *stream, ps_state **out) {
     st->tun = resolve_tuning(nullptr, dtype);
     cudaError_t e = cudaGetDevice(&st->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&st->num_sms, cudaDevAttrMultiProcessorCount, st->device);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&st->stage_done, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaMalloc((void **)&st->partials, 2 * sizeof(double) * (size_t)reduce_blocks());
     if (e == cudaSuccess) e = cudaMalloc((void **)&st->rout, 2 * sizeof(double));
     if (e == cudaSuccess) e = cudaMallocHost((void **)&st->hout, 2 * sizeof(double));
@@ -350,9 +334,6 @@ void ps_destroy(ps_state *st) {
         cudaEventDestroy(t.b);
     }
     for (auto e : st->event_pool) cudaEventDestroy(e);
-    if (st->stage_done) cudaEventDestroy(st->stage_done);
-    if (st->dplan) cudaFree(st->dplan);
-    if (st->hstage) cudaFreeHost(st->hstage);
     if (st->partials) cudaFree(st->partials);
     if (st->rout) cudaFree(st->rout);
     if (st->hout) cudaFreeHost(st->hout);
@@ -420,15 +401,6 @@ int ps_plan_create(int n, int dtype, const uint64_t *x, const uint64_t *z, const
         delete pl;
         return fail(rc, err);
     }
-    pack_plan(pl->plan, pl->img);
-    cudaError_t e = cudaGetDevice(&pl->device);
-    if (e == cudaSuccess) e = cudaMalloc(&pl->dev, pl->img.bytes.size());
-    if (e == cudaSuccess) e = cudaMemcpy(pl->dev, pl->img.bytes.data(), pl->img.bytes.size(), cudaMemcpyHostToDevice);
-    if (e != cudaSuccess) {
-        if (pl->dev) cudaFree(pl->dev);
-        delete pl;
-        return cuda_fail(e, "ps_plan_create upload");
-    }
     *out = pl;
     return PS_OK;
 }
@@ -437,9 +409,8 @@ int ps_plan_apply(ps_state *st, const ps_plan *plan) {
     if (int rc = check_state(st)) return rc;
     if (!plan) return fail(PS_ERR_ARG, "null plan");
     if (plan->plan.n != st->n || plan->plan.dtype != st->dtype) return fail(PS_ERR_ARG, "plan built for another n or dtype");
-    if (plan->device != st->device) return fail(PS_ERR_ARG, "plan resides on another device");
     DeviceGuard g(st->device);
-    return launch_plan(st, plan->plan, plan->img, plan->dev);
+    return launch_plan(st, plan->plan);
 }
 
 static void fill_info(const Plan &p, ps_plan_info *out) {
@@ -465,14 +436,7 @@ int ps_plan_get_info(const ps_plan *plan, ps_plan_info *out) {
     return PS_OK;
 }
 
-void ps_plan_destroy(ps_plan *plan) {
-    if (!plan) return;
-    if (plan->dev) {
-        DeviceGuard g(plan->device);
-        cudaFree(plan->dev);
-    }
-    delete plan;
-}
+void ps_plan_destroy(ps_plan *plan) { delete plan; }
 
 int ps_plan_describe(int n, int dtype, const uint64_t *x, const uint64_t *z, const double *phi, size_t count,
                      const ps_tuning *tuning, ps_plan_info *out) {

@@ -11,7 +11,7 @@
 namespace ps {
 
 constexpr int kMaxD = 16;       // most basis vectors of one window (tile coordinates above c)
-constexpr int kMaxG = 4;        // most group bits in the register stage
+constexpr int kMaxG = 5;        // most group bits in the register stage
 constexpr int kMaxWindow = 256; // most rotations per window
 constexpr int kMaxN = 40;
 
@@ -30,7 +30,7 @@ struct RotDesc {
     uint64_t z;          // global Z mask (coset sign)
     uint64_t x;          // global X mask (pair kernel)
     uint32_t zt;         // Z mask in tile coordinates
-    uint16_t smask;      // bit m: parity(U(m) & zt), U(m) = combination m of the group basis
+    uint32_t smask;      // bit m: parity(U(m) & zt), U(m) = combination m of the group basis
     uint8_t mu;          // X mask in group coordinates
     uint8_t flags;       // bit 0: popc(x & z) & 1; bit 1: full form
 };
@@ -38,9 +38,13 @@ struct RotDesc {
 // A register-stage round inside a tile window: every thread owns groups of
 // 2^G tile amplitudes {j0 ^ U(m)}, U(m) = XOR of u[i] over the set bits i
 // of m, and applies rotations [rot_off, rot_off + nrot) to them in registers.
+// The basis u keeps the rounds' own X masks (so an independent rotation has a
+// single-bit group mask); the coset representatives j0 have zeros at the
+// pivots of the span's echelon form.
 struct SubDesc {
-    uint32_t u[kMaxG];   // group basis in tile coordinates; u[i]'s top bit is piv_of[i]
-    int8_t piv[kMaxG];   // pivot positions sorted ascending (coset representatives have zeros there)
+    uint32_t u[kMaxG];   // group basis in tile coordinates
+    int8_t piv[kMaxG];   // echelon pivot positions of span(u), sorted ascending
+    int8_t pad[3];
     int32_t rot_off;
     int32_t nrot;
 };
@@ -91,21 +95,55 @@ struct Ham {
 
 void set_error(const std::string &msg);
 
-// Kernel launchers (ps_kernels.cu).  Each returns a cudaError_t as int.
-struct DevPlanView {
-    const WinDesc *win;
-    const SubDesc *sub;
-    const RotDesc *rot;
+// ---------------------------------------------------------------- launches
+// Every pass receives its window by value in the kernel's parameter space,
+// so a CTA computes its tile addresses and issues its loads without first
+// reading descriptors from global memory.
+
+constexpr int kParamRot = 32;  // most rotations of a tile window
+constexpr int kParamSub = 16;  // most register rounds of a tile window
+
+struct TileRotP {
+    double base;     // signed tan(phi) or sin(phi) (see RotDesc)
+    double c;        // cos(phi) for the full form
+    uint64_t z;      // global Z mask
+    uint32_t zt;     // Z mask in tile coordinates
+    uint32_t smask;  // bit m: parity(U(m) & zt)
+    uint32_t meta;   // bits 0-4 group X mask mu, bit 5 popc(x & z) & 1, bit 6 full form
+    uint32_t pad;
 };
-// `scale` multiplies every amplitude of the pass after its rotations (the
-// part of the accumulated cos(phi) factors the state stores).
-int launch_tile(int dtype, int G, int ng_request, void *psi, int n, int B, const DevPlanView &dp, const WinDesc &hw,
-                int wi, double scale, void *stream);
-int launch_pair(int dtype, void *psi, int n, const DevPlanView &dp, const WinDesc &hw, int wi, double scale,
-                void *stream, int num_sms);
+
+struct TileSubP {
+    uint32_t u[kMaxG];  // group basis in tile coordinates
+    int8_t piv[kMaxG];  // echelon pivots of span(u), ascending
+    uint8_t r0, r1;     // rotations [r0, r1) of the window
+    uint8_t fast;       // k > 0: the round is k tangent-form rotations with an even number
+                        // of Y factors whose group X masks are 1, 2, 4, ..., 2^(k-1) in order
+};
+
+struct TileParams {
+    uint64_t v[kMaxD];  // window basis, v[i] <-> tile bit c + i
+    int8_t piv[kMaxD];  // pivots of v, ascending
+    int32_t c, d, nsub, nrot;
+    TileSubP sub[kParamSub];
+    TileRotP rot[kParamRot];
+};
+
+struct PairParams {
+    uint64_t x, z;
+    double base, c;
+    uint32_t flags;  // bit 0 popc(x & z) & 1, bit 1 full form
+    uint32_t pad;
+};
+
+// After its rotations a pass applies a <- a + kdelta * a to every amplitude:
+// the part of the accumulated cos(phi) factors the state stores.
+int launch_tile(int dtype, int G, int ng_request, void *psi, int n, const TileParams &tp, double kdelta,
+                void *stream);
+int launch_pair(int dtype, void *psi, int n, const PairParams &pp, double kdelta, void *stream, int num_sms);
 int launch_reduce(int dtype, int what, const void *a, const void *b, int n, double *partials, double *out_dev,
                   void *stream);
 int reduce_blocks();
-int prepare_kernels(int dtype, int G, int B);
+int prepare_kernels(int dtype);
 
 }  // namespace ps

@@ -91,38 +91,74 @@ void fill_coeffs(RotDesc &r, uint64_t x, uint64_t z, double phi) {
 // cos(phi) of a tangent-form rotation (1 for the full form).
 double tangent_scale(const RotDesc &r, double phi) { return (r.flags & 2) ? 1.0 : std::cos(phi); }
 
+// A span given by explicit basis vectors u (kept as given) together with
+// an echelon form used to reduce and to pick pivots; emask[j] says which
+// u's make up echelon vector j, so reduction yields coordinates in u.
+struct Span {
+    std::vector<uint64_t> u, ech;
+    std::vector<uint32_t> emask;
+    uint64_t reduce(uint64_t v, uint32_t *coords) const {
+        std::vector<int> order(ech.size());
+        for (size_t i = 0; i < ech.size(); ++i) order[i] = (int)i;
+        std::sort(order.begin(), order.end(), [&](int a, int b) { return top_bit(ech[a]) > top_bit(ech[b]); });
+        uint32_t cm = 0;
+        for (int i : order)
+            if ((v >> top_bit(ech[i])) & 1) {
+                v ^= ech[i];
+                cm ^= emask[i];
+            }
+        if (coords) *coords = cm;
+        return v;
+    }
+    bool add(uint64_t v) {
+        uint32_t cm = 0;
+        uint64_t r = reduce(v, &cm);
+        if (r == 0) return false;
+        u.push_back(v);
+        ech.push_back(r);
+        emask.push_back(cm ^ (1u << (u.size() - 1)));
+        return true;
+    }
+    bool has_pivot(int pos) const {
+        for (uint64_t e : ech)
+            if (top_bit(e) == pos) return true;
+        return false;
+    }
+    size_t rank() const { return u.size(); }
+};
+
 // Build the register-stage rounds of one tile window (rotations [a, b) of
 // the plan, tile-local masks already in xt / zt).
-void build_subwindows(Plan &p, WinDesc &w, const std::vector<uint32_t> &xt, const std::vector<uint32_t> &zt,
-                      int B, int G) {
+// Returns the number of rotations covered (fewer than w.nrot only when the
+// window would need more than kParamSub rounds).
+size_t build_subwindows(Plan &p, WinDesc &w, const std::vector<uint32_t> &xt, const std::vector<uint32_t> &zt,
+                        int B, int G) {
     size_t a = w.rot_off, b = (size_t)w.rot_off + w.nrot;
     w.sub_off = (int32_t)p.sub.size();
     w.nsub = 0;
     size_t j = a;
-    while (j < b) {
-        Echelon gb;
+    while (j < b && w.nsub < kParamSub) {
+        Span gb;
         size_t start = j;
         while (j < b) {
             uint64_t v = xt[j - a];
-            if (v && gb.reduce(v) != 0) {
+            if (v && gb.reduce(v, nullptr) != 0) {
                 if ((int)gb.rank() >= G) break;
-                gb.add_if_new(v);
+                gb.add(v);
             }
             ++j;
         }
         // pad with unit vectors at the highest free positions (keeps the
         // lane-varying low bits of the coset representatives contiguous)
-        std::vector<int> pivs;
-        for (uint64_t v : gb.vec) pivs.push_back(top_bit(v));
-        for (int pos = B - 1; (int)gb.rank() < G && pos >= 0; --pos) {
-            if (std::find(pivs.begin(), pivs.end(), pos) != pivs.end()) continue;
-            gb.vec.push_back(1ull << pos);
-            pivs.push_back(pos);
-        }
+        for (int pos = B - 1; (int)gb.rank() < G && pos >= 0; --pos)
+            if (!gb.has_pivot(pos)) gb.add(1ull << pos);
         SubDesc sd;
         std::memset(&sd, 0, sizeof(sd));
-        for (int i = 0; i < G; ++i) sd.u[i] = (uint32_t)gb.vec[i];
-        std::vector<int> sorted = pivs;
+        std::vector<int> sorted;
+        for (int i = 0; i < G; ++i) {
+            sd.u[i] = (uint32_t)gb.u[i];
+            sorted.push_back(top_bit(gb.ech[i]));
+        }
         std::sort(sorted.begin(), sorted.end());
         for (int i = 0; i < G; ++i) sd.piv[i] = (int8_t)sorted[i];
         sd.rot_off = (int32_t)start;
@@ -130,8 +166,7 @@ void build_subwindows(Plan &p, WinDesc &w, const std::vector<uint32_t> &xt, cons
         // per-rotation group coordinates and sign masks
         for (size_t r = start; r < j; ++r) {
             uint32_t coords = 0;
-            uint64_t rem = gb.reduce(xt[r - a], &coords);
-            (void)rem;  // zero by construction
+            gb.reduce(xt[r - a], &coords);  // remainder is zero by construction
             RotDesc &rd = p.rot[r];
             rd.mu = (uint8_t)coords;
             rd.zt = zt[r - a];
@@ -142,11 +177,12 @@ void build_subwindows(Plan &p, WinDesc &w, const std::vector<uint32_t> &xt, cons
                     if ((m >> i) & 1) U ^= sd.u[i];
                 sm |= (uint32_t)(__builtin_popcount(U & rd.zt) & 1) << m;
             }
-            rd.smask = (uint16_t)sm;
+            rd.smask = sm;
         }
         p.sub.push_back(sd);
         ++w.nsub;
     }
+    return j - a;
 }
 
 }  // namespace
@@ -158,7 +194,7 @@ Tuning resolve_tuning(const ps_tuning *t, int dtype) {
     r.max_window = (t && t->max_window) ? t->max_window : 64;
     r.pair_single = (t && t->pair_single) ? t->pair_single : 1;
     r.kernel_timing = t ? t->kernel_timing : 0;
-    r.reg_groups = t ? t->reg_groups : 0;
+    r.reg_groups = (t && t->reg_groups) ? t->reg_groups : (dtype == PS_C64 ? 4 : 2);
     return r;
 }
 
@@ -170,9 +206,10 @@ int build_plan(int n, int dtype, const uint64_t *x, const uint64_t *z, const dou
     };
     if (n < 1 || n > kMaxN) return fail("n must be in [1, 40]");
     if (dtype != PS_C64 && dtype != PS_C128) return fail("dtype must be PS_C64 or PS_C128");
-    int Bmax = dtype == PS_C64 ? 14 : 13;
+    int Bmax = dtype == PS_C64 ? 13 : 12;  // two 64 KB tile buffers plus records fit in shared memory
     if (tun.B < 6 || tun.B > Bmax) return fail("tile_bits out of range");
-    if (tun.G < 1 || tun.G > kMaxG) return fail("group_bits must be in [1, 4]");
+    if (tun.G < 1 || tun.G > (dtype == PS_C64 ? kMaxG : kMaxG - 1))
+        return fail("group_bits must be in [1, 5] for PS_C64 and [1, 4] for PS_C128");
     if (tun.max_window < 1 || tun.max_window > kMaxWindow) return fail("max_window must be in [1, 256]");
     if (tun.pair_single != 1 && tun.pair_single != 2) return fail("pair_single must be 0, 1 or 2");
     if (tun.reg_groups != 0 && tun.reg_groups != 1 && tun.reg_groups != 2 && tun.reg_groups != 4)
@@ -211,10 +248,10 @@ int build_plan(int n, int dtype, const uint64_t *x, const uint64_t *z, const dou
         size_t start = j;
         if (B == n) {
             // the whole state is one tile
-            j = std::min(count, start + (size_t)tun.max_window);
+            j = std::min(count, start + (size_t)std::min(tun.max_window, kParamRot));
         } else {
             Echelon hb;
-            while (j < count && j - start < (size_t)tun.max_window) {
+            while (j < count && j - start < (size_t)std::min(tun.max_window, kParamRot)) {
                 uint64_t v = x[j] >> cmin;
                 if (v && hb.reduce(v) != 0) {
                     if ((int)hb.rank() + 1 > B - cmin) break;
@@ -228,7 +265,6 @@ int build_plan(int n, int dtype, const uint64_t *x, const uint64_t *z, const dou
         w.rot_off = (int32_t)start;
         w.nrot = (int32_t)(j - start);
         w.kprod = 1.0;
-        for (size_t r = start; r < j; ++r) w.kprod *= tangent_scale(p.rot[r], phi[r]);
         bool single_pair = (w.nrot == 1 && x[start] != 0 && tun.pair_single == 1 && n >= 2);
         if (single_pair) {
             w.kind = 1;
@@ -238,6 +274,7 @@ int build_plan(int n, int dtype, const uint64_t *x, const uint64_t *z, const dou
             w.piv[0] = (int8_t)top_bit(x[start]);
             w.sub_off = (int32_t)p.sub.size();
             w.nsub = 0;
+            w.kprod = tangent_scale(p.rot[start], phi[start]);
             p.win.push_back(w);
             continue;
         }
@@ -282,7 +319,12 @@ int build_plan(int n, int dtype, const uint64_t *x, const uint64_t *z, const dou
                 ztile |= (uint32_t)(__builtin_popcountll(w.v[i] & z[r]) & 1) << (c + i);
             zt[r - start] = ztile;
         }
-        build_subwindows(p, w, xt, zt, B, G);
+        const size_t covered = build_subwindows(p, w, xt, zt, B, G);
+        if (covered < (size_t)w.nrot) {
+            w.nrot = (int32_t)covered;
+            j = start + covered;
+        }
+        for (size_t r = start; r < j; ++r) w.kprod *= tangent_scale(p.rot[r], phi[r]);
         p.win.push_back(w);
     }
     return PS_OK;

@@ -12,16 +12,16 @@ constexpr int kPairThreads = 256;
 // amplitudes j, j+1 (one 16-byte vector, bit h = top bit of x clear in j) and
 // their partners j^x, (j+1)^x (one 16-byte vector at (j^x) & ~1, element
 // order swapped when x is odd); x == 1 pairs the two halves of one vector.
-// Arithmetic identical to the tile kernel: a' = scale * (cc a + t rotY(b)).
+// Arithmetic identical to the tile kernel: o = cc a + t rotY(b), then o + kdelta * o.
 template <bool FULL, bool YODD>
 __device__ __forceinline__ void pair_c64_body(float4 *__restrict__ v, int n, uint64_t x, uint64_t z, float base,
-                                              float cc, float scale) {
+                                              float cc, float kdelta) {
     const uint64_t stride = (uint64_t)gridDim.x * kPairThreads;
-    const bool do_scale = scale != 1.0f;
+    const bool do_scale = kdelta != 0.0f;
     auto fin = [&](float2 o) {
         if (do_scale) {
-            o.x *= scale;
-            o.y *= scale;
+            o.x = fmaf(kdelta, o.x, o.x);
+            o.y = fmaf(kdelta, o.y, o.y);
         }
         return o;
     };
@@ -70,28 +70,28 @@ __device__ __forceinline__ void pair_c64_body(float4 *__restrict__ v, int n, uin
     }
 }
 
-__global__ void __launch_bounds__(kPairThreads) k_pair_c64(float2 *__restrict__ psi, int n, DevPlanView dp, int wi,
-                                                           float scale) {
-    const RotDesc rd = dp.rot[dp.win[wi].rot_off];
+__global__ void __launch_bounds__(kPairThreads) k_pair_c64(float2 *__restrict__ psi, int n, const PairParams pp,
+                                                           float kdelta) {
     float4 *v = reinterpret_cast<float4 *>(psi);
-    const bool full = rd.flags & 2, yodd = rd.flags & 1;
+    const bool full = pp.flags & 2, yodd = pp.flags & 1;
+    const float base = (float)pp.base, cc = (float)pp.c;
     if (full) {
-        if (yodd) pair_c64_body<true, true>(v, n, rd.x, rd.z, rd.base32, rd.c32, scale);
-        else pair_c64_body<true, false>(v, n, rd.x, rd.z, rd.base32, rd.c32, scale);
+        if (yodd) pair_c64_body<true, true>(v, n, pp.x, pp.z, base, cc, kdelta);
+        else pair_c64_body<true, false>(v, n, pp.x, pp.z, base, cc, kdelta);
     } else {
-        if (yodd) pair_c64_body<false, true>(v, n, rd.x, rd.z, rd.base32, 1.0f, scale);
-        else pair_c64_body<false, false>(v, n, rd.x, rd.z, rd.base32, 1.0f, scale);
+        if (yodd) pair_c64_body<false, true>(v, n, pp.x, pp.z, base, 1.0f, kdelta);
+        else pair_c64_body<false, false>(v, n, pp.x, pp.z, base, 1.0f, kdelta);
     }
 }
 
 // Single non-diagonal rotation, complex128: one 16-byte amplitude and its partner per unit.
 template <bool FULL, bool YODD>
 __device__ __forceinline__ void pair_c128_body(double2 *__restrict__ psi, int n, uint64_t x, uint64_t z, double base,
-                                               double cc, double scale) {
+                                               double cc, double kdelta) {
     const int h = 63 - __clzll(x);
     const uint64_t units = 1ull << (n - 1);
     const uint64_t stride = (uint64_t)gridDim.x * kPairThreads;
-    const bool do_scale = scale != 1.0;
+    const bool do_scale = kdelta != 0.0;
     for (uint64_t u = (uint64_t)blockIdx.x * kPairThreads + threadIdx.x; u < units; u += stride) {
         const uint64_t j = insert_zero(u, h);
         const uint64_t pj = j ^ x;
@@ -100,26 +100,25 @@ __device__ __forceinline__ void pair_c128_body(double2 *__restrict__ psi, int n,
         double2 na = rot_update<double, FULL, YODD>(a, b, t, cc);
         double2 nb = rot_update<double, FULL, YODD>(b, a, YODD ? -t : t, cc);
         if (do_scale) {
-            na.x *= scale;
-            na.y *= scale;
-            nb.x *= scale;
-            nb.y *= scale;
+            na.x = fma(kdelta, na.x, na.x);
+            na.y = fma(kdelta, na.y, na.y);
+            nb.x = fma(kdelta, nb.x, nb.x);
+            nb.y = fma(kdelta, nb.y, nb.y);
         }
         psi[j] = na;
         psi[pj] = nb;
     }
 }
 
-__global__ void __launch_bounds__(kPairThreads) k_pair_c128(double2 *__restrict__ psi, int n, DevPlanView dp, int wi,
-                                                            double scale) {
-    const RotDesc rd = dp.rot[dp.win[wi].rot_off];
-    const bool full = rd.flags & 2, yodd = rd.flags & 1;
+__global__ void __launch_bounds__(kPairThreads) k_pair_c128(double2 *__restrict__ psi, int n, const PairParams pp,
+                                                            double kdelta) {
+    const bool full = pp.flags & 2, yodd = pp.flags & 1;
     if (full) {
-        if (yodd) pair_c128_body<true, true>(psi, n, rd.x, rd.z, rd.base64, rd.c64, scale);
-        else pair_c128_body<true, false>(psi, n, rd.x, rd.z, rd.base64, rd.c64, scale);
+        if (yodd) pair_c128_body<true, true>(psi, n, pp.x, pp.z, pp.base, pp.c, kdelta);
+        else pair_c128_body<true, false>(psi, n, pp.x, pp.z, pp.base, pp.c, kdelta);
     } else {
-        if (yodd) pair_c128_body<false, true>(psi, n, rd.x, rd.z, rd.base64, 1.0, scale);
-        else pair_c128_body<false, false>(psi, n, rd.x, rd.z, rd.base64, 1.0, scale);
+        if (yodd) pair_c128_body<false, true>(psi, n, pp.x, pp.z, pp.base, 1.0, kdelta);
+        else pair_c128_body<false, false>(psi, n, pp.x, pp.z, pp.base, 1.0, kdelta);
     }
 }
 
@@ -196,18 +195,16 @@ __global__ void __launch_bounds__(kReduceThreads) k_reduce2(const double *__rest
 
 int reduce_blocks() { return kReduceBlocks; }
 
-int launch_pair(int dtype, void *psi, int n, const DevPlanView &dp, const WinDesc &hw, int wi, double scale,
-                void *stream, int num_sms) {
-    (void)hw;
+int launch_pair(int dtype, void *psi, int n, const PairParams &pp, double kdelta, void *stream, int num_sms) {
     cudaStream_t st = (cudaStream_t)stream;
     const uint64_t units = 1ull << (n - 1);
     const uint64_t want = (units + kPairThreads - 1) / kPairThreads;
     const uint64_t cap = (uint64_t)num_sms * 8;
     const unsigned grid = (unsigned)(want < cap ? want : cap);
     if (dtype == PS_C64)
-        k_pair_c64<<<grid, kPairThreads, 0, st>>>((float2 *)psi, n, dp, wi, (float)scale);
+        k_pair_c64<<<grid, kPairThreads, 0, st>>>((float2 *)psi, n, pp, (float)kdelta);
     else
-        k_pair_c128<<<grid, kPairThreads, 0, st>>>((double2 *)psi, n, dp, wi, scale);
+        k_pair_c128<<<grid, kPairThreads, 0, st>>>((double2 *)psi, n, pp, kdelta);
     return (int)cudaGetLastError();
 }
 

@@ -79,11 +79,11 @@ def test_plan_validation():
     with pytest.raises(ps.PsError):
         ps.ps_plan_describe(8, ps.PS_C64, [1], [0], [float("inf")])
     with pytest.raises(ps.PsError):
-        ps.ps_plan_describe(20, ps.PS_C64, [1], [0], [0.1], {"tile_bits": 15})
+        ps.ps_plan_describe(20, ps.PS_C64, [1], [0], [0.1], {"tile_bits": 14})
     with pytest.raises(ps.PsError):
-        ps.ps_plan_describe(20, ps.PS_C128, [1], [0], [0.1], {"tile_bits": 14})
+        ps.ps_plan_describe(20, ps.PS_C128, [1], [0], [0.1], {"tile_bits": 13})
     with pytest.raises(ps.PsError):
-        ps.ps_plan_describe(20, ps.PS_C64, [1], [0], [0.1], {"group_bits": 5})
+        ps.ps_plan_describe(20, ps.PS_C64, [1], [0], [0.1], {"group_bits": 6})
     with pytest.raises(ps.PsError):
         ps.ps_plan_describe(20, ps.PS_C64, [1], [0], [0.1], {"max_window": 300})
     info = ps.ps_plan_describe(20, ps.PS_C64, [], [], [])
