@@ -194,7 +194,7 @@ Tuning resolve_tuning(const ps_tuning *t, int dtype) {
     r.max_window = (t && t->max_window) ? t->max_window : 64;
     r.pair_single = (t && t->pair_single) ? t->pair_single : 1;
     r.kernel_timing = t ? t->kernel_timing : 0;
-    r.reg_groups = (t && t->reg_groups) ? t->reg_groups : (dtype == PS_C64 ? 4 : 2);
+    r.reg_groups = (t && t->reg_groups) ? t->reg_groups : 2;
     return r;
 }
 

@@ -150,8 +150,15 @@ __device__ __forceinline__ uint64_t v_of(const TileParams &P, uint32_t x) {
 // straight to HBM, using idx(j0 ^ U(m)) = idx(j0) ^ W(m), W(m) = XOR of
 // W_i = V(u_i >> c) ^ (u_i & (2^c - 1)) over the bits i of m.  Group members
 // are visited in Gray-code order m = i ^ (i >> 1), one XOR per address.
+// Resident CTAs per SM the register budget is sized for: three when a thread
+// holds at most 16 complex64 (8 complex128) amplitudes, else two.
 template <typename R, int G, int NG>
-__global__ void __launch_bounds__(kTileThreads, 2) k_tile(typename CT<R>::T *__restrict__ psi,
+constexpr int tile_min_blocks() {
+    return (NG << G) * (int)sizeof(R) <= 64 ? 3 : 2;
+}
+
+template <typename R, int G, int NG>
+__global__ void __launch_bounds__(kTileThreads, tile_min_blocks<R, G, NG>()) k_tile(typename CT<R>::T *__restrict__ psi,
                                                           const __grid_constant__ TileParams P, R kdelta) {
     using C = typename CT<R>::T;
     constexpr int LS = sizeof(C) == 8 ? 3 : 4;  // log2 bytes per amplitude
