@@ -188,6 +188,28 @@ int ps_norm(ps_state *st, double *out);
  * work runs on psi's stream and synchronises it. */
 int ps_overlap(const ps_state *psi0, ps_state *psi, double out[2]);
 
+/* Allocation-free overlap.  The paper has no counterpart of this call; it is
+ * for callers that cannot allocate device memory -- cudaMalloc and cudaFree
+ * synchronise the whole device and fail once another allocator (for example
+ * a framework's caching allocator, or a budget fixed at start-up) owns the
+ * memory, so code that must not stall or that lives inside such a framework
+ * has to work with the buffers it already holds.  Unlike ps_overlap it needs
+ * no handle (ps_create allocates) and allocates nothing: its partial sums use
+ * a fixed device array inside the library (1216 x 2 doubles, about 19 KB,
+ * held on every GPU that loads the library until the process exits).
+ *
+ * Writes <psi0|psi> = sum_k conj(psi0[k]) psi[k] of the stored amplitudes
+ * (FP64, same fixed summation order as ps_overlap) as two doubles (re, im) to
+ * the caller's device memory out_dev.  psi0_dev, psi_dev: 2^n amplitudes of
+ * dtype, 16-byte aligned, on the current device.  Asynchronous on `stream`.
+ * n outside [1, 40] (the range the fixed scratch serves) gives PS_ERR_ARG.
+ * The first call on a device looks up the scratch array's device address
+ * (one cudaGetSymbolAddress); make that first call before any stream
+ * capture.  All calls share the one array: calls that can run at the same
+ * time on the GPU (different streams without ordering) race and give wrong
+ * results.  Nothing needs clearing between calls. */
+int ps_overlap_noalloc(int n, int dtype, const void *psi0_dev, const void *psi_dev, void *stream, double *out_dev);
+
 /* ----------------------------------------------------------- Hamiltonians */
 
 /* Copy a term list H = sum_l h[l] P_l (Eq. 2, Methods, "Hamiltonian

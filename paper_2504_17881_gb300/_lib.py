@@ -72,6 +72,7 @@ _SIGS = {
     "ps_norm": (_i, [_vp, ctypes.POINTER(_d)]),
     "ps_get_scale": (_i, [_vp, ctypes.POINTER(_d)]),
     "ps_overlap": (_i, [_vp, _vp, _vp]),
+    "ps_overlap_noalloc": (_i, [_i, _i, _vp, _vp, _vp, _vp]),
     "ps_ham_create": (_i, [_i, _sz, _vp, _vp, _vp, _pp]),
     "ps_ham_destroy": (None, [_vp]),
     "ps_ham_lambda": (_d, [_vp]),
@@ -234,6 +235,12 @@ def ps_overlap(h0: int, h: int) -> complex:
     out = (ctypes.c_double * 2)()
     _check(lib.ps_overlap(ctypes.c_void_p(h0), ctypes.c_void_p(h), out))
     return complex(out[0], out[1])
+
+
+def ps_overlap_noalloc(n: int, dtype: int, psi0_ptr: int, psi_ptr: int, stream: int | None, out_ptr: int):
+    """<psi0|psi> of two device buffers into 2 doubles at device address out_ptr (asynchronous)."""
+    _check(lib.ps_overlap_noalloc(n, dtype, ctypes.c_void_p(psi0_ptr), ctypes.c_void_p(psi_ptr),
+                                  ctypes.c_void_p(stream or 0), ctypes.c_void_p(out_ptr)))
 
 
 def ps_ham_create(n: int, x, z, h) -> int:
