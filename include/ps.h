@@ -88,6 +88,7 @@ typedef struct ps_plan_info {
     uint64_t tile_windows;    /* passes run by the fused tile kernel */
     uint64_t pair_windows;    /* passes run by the pair-streaming kernel */
     uint64_t subwindows;      /* register-stage rounds summed over tile windows */
+    uint64_t fast_subwindows; /* rounds of the standard shape (straight-line code path) */
     uint64_t max_window;      /* longest window (rotations) */
     int tile_bits;            /* B actually used (min(B, n)) */
     int group_bits;           /* G actually used */

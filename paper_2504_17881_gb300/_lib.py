@@ -39,7 +39,8 @@ class ps_stats(ctypes.Structure):
 
 class ps_plan_info(ctypes.Structure):
     _fields_ = [("rotations", ctypes.c_uint64), ("windows", ctypes.c_uint64), ("tile_windows", ctypes.c_uint64),
-                ("pair_windows", ctypes.c_uint64), ("subwindows", ctypes.c_uint64), ("max_window", ctypes.c_uint64),
+                ("pair_windows", ctypes.c_uint64), ("subwindows", ctypes.c_uint64),
+                ("fast_subwindows", ctypes.c_uint64), ("max_window", ctypes.c_uint64),
                 ("tile_bits", ctypes.c_int), ("group_bits", ctypes.c_int)]
 
 

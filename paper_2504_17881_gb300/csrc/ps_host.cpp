@@ -55,12 +55,7 @@ static void fill_tile_params(const Plan &p, const WinDesc &w, TileParams &tp) {
         }
         tp.sub[s].r0 = (uint8_t)(sd.rot_off - w.rot_off);
         tp.sub[s].r1 = (uint8_t)(sd.rot_off - w.rot_off + sd.nrot);
-        bool fast = sd.nrot >= 1 && sd.nrot <= p.G;
-        for (int r = 0; r < sd.nrot && fast; ++r) {
-            const RotDesc &rd = p.rot[sd.rot_off + r];
-            fast = rd.mu == (1u << r) && rd.flags == 0;
-        }
-        tp.sub[s].fast = fast ? (uint8_t)sd.nrot : 0;
+        tp.sub[s].fast = sd.fast;
     }
     for (int r = 0; r < w.nrot; ++r) {
         const RotDesc &rd = p.rot[w.rot_off + r];
@@ -423,6 +418,7 @@ static void fill_info(const Plan &p, ps_plan_info *out) {
         else {
             out->tile_windows++;
             out->subwindows += (uint64_t)w.nsub;
+            for (int si = 0; si < w.nsub; ++si) out->fast_subwindows += p.sub[w.sub_off + si].fast ? 1 : 0;
         }
         out->max_window = std::max<uint64_t>(out->max_window, (uint64_t)w.nrot);
     }

@@ -44,7 +44,8 @@ struct RotDesc {
 struct SubDesc {
     uint32_t u[kMaxG];   // group basis in tile coordinates
     int8_t piv[kMaxG];   // echelon pivot positions of span(u), sorted ascending
-    int8_t pad[3];
+    uint8_t fast;        // k > 0: a standard round of k rotations (see TileSubP::fast)
+    int8_t pad[2];
     int32_t rot_off;
     int32_t nrot;
 };

@@ -179,6 +179,12 @@ size_t build_subwindows(Plan &p, WinDesc &w, const std::vector<uint32_t> &xt, co
             }
             rd.smask = sm;
         }
+        bool fast = sd.nrot >= 1 && sd.nrot <= G;
+        for (int r = 0; r < sd.nrot && fast; ++r) {
+            const RotDesc &rd = p.rot[sd.rot_off + r];
+            fast = rd.mu == (1u << r) && rd.flags == 0;
+        }
+        sd.fast = fast ? (uint8_t)sd.nrot : 0;
         p.sub.push_back(sd);
         ++w.nsub;
     }

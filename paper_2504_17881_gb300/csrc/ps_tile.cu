@@ -9,6 +9,8 @@
 //     straight back, so shared memory only carries the tile between rounds;
 //   * tangent-form updates: two fused multiply-adds per amplitude and rotation
 //     plus one sign XOR per pair.
+#include <type_traits>
+
 #include "ps_device.cuh"
 #include "ps_internal.h"
 
@@ -16,10 +18,11 @@ namespace ps {
 
 // Per-rotation record in shared memory, built by each CTA from RotDesc:
 //   coef[i]  signed coefficient of pair base i (or amplitude i when mu == 0):
-//            base * (-1)^{parity(U(m) & zt)} for the group index m it stands for;
+//            base * (-1)^{parity(U(m) & zt) + parity(k0 & z)} for the group index m;
 //   z        global Z mask (the coset sign parity(k0 & z) of the tile);
 //   zt       Z mask in tile coordinates;  c  cos(phi) for the full form;
 //   meta     bits 0-4 mu, bit 5 popc(x & z) & 1, bit 6 full form.
+// The coefficients already carry the coset sign parity(k0 & z) of the CTA.
 template <typename R> struct KRot;
 template <> struct __align__(16) KRot<float> {
     float coef[32];
@@ -89,29 +92,61 @@ __device__ __forceinline__ void rot_dispatch(int code, typename CT<R>::T (&a)[NG
 // Standard round: K tangent-form rotations with an even number of Y factors
 // whose group X masks are 1, 2, ..., 2^(K-1) in order, as straight-line code
 // (no per-rotation dispatch), so registers are renamed freely between updates.
+// Coefficients 0..NC-1 of a record, read as 16-byte vectors.
+template <typename R, int NC>
+__device__ __forceinline__ void load_coefs(const KRot<R> &k, R (&cf)[NC]) {
+    constexpr int PER = 16 / (int)sizeof(R);
+    if constexpr (NC >= PER) {
+#pragma unroll
+        for (int v = 0; v < NC / PER; ++v) {
+            if constexpr (sizeof(R) == 4) {
+                const float4 q = reinterpret_cast<const float4 *>(k.coef)[v];
+                cf[4 * v] = q.x;
+                cf[4 * v + 1] = q.y;
+                cf[4 * v + 2] = q.z;
+                cf[4 * v + 3] = q.w;
+            } else {
+                const double2 q = reinterpret_cast<const double2 *>(k.coef)[v];
+                cf[2 * v] = q.x;
+                cf[2 * v + 1] = q.y;
+            }
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < NC; ++q) cf[q] = k.coef[q];
+    }
+}
+
+// Standard round: K tangent-form rotations with an even number of Y factors
+// whose group X masks are 1, 2, ..., 2^(K-1) in order, as straight-line code
+// (no per-rotation dispatch), so registers are renamed freely between
+// updates.  Per rotation and group the 2^(G-1) pair coefficients take the
+// group's sign parity(j0 & zt) once.
 template <typename R, int G, int NG, int K>
 __device__ __forceinline__ void fast_round(typename CT<R>::T (&a)[NG][1 << G], const KRot<R> *kr,
-                                           const uint32_t (&j0)[NG], uint64_t k0) {
+                                           const uint32_t (&j0)[NG]) {
     using C = typename CT<R>::T;
+    constexpr int NC = 1 << (G - 1);
 #pragma unroll
     for (int i = 0; i < K; ++i) {
         const KRot<R> &k = kr[i];
         const uint32_t zt = k.zt;
-        const uint32_t tpar = (uint32_t)__popcll(k0 & k.z);
-        R cf[1 << (G - 1)];
-#pragma unroll
-        for (int q = 0; q < (1 << (G - 1)); ++q) cf[q] = k.coef[q];
+        R cf[NC];
+        load_coefs<R, NC>(k, cf);
 #pragma unroll
         for (int g = 0; g < NG; ++g) {
-            const uint32_t sw = ((__popc(j0[g] & zt) ^ tpar) & 1u) << 31;
+            const uint32_t sw = (uint32_t)__popc(j0[g] & zt) << 31;
+            R t[NC];
+#pragma unroll
+            for (int q = 0; q < NC; ++q) t[q] = xsign(cf[q], sw);
 #pragma unroll
             for (int m = 0; m < (1 << G); ++m) {
                 if (((m >> i) & 1) == 0) {
                     const int p = m | (1 << i);
-                    const R t = xsign(cf[(m & ((1 << i) - 1)) | ((m >> (i + 1)) << i)], sw);
+                    const R tq = t[(m & ((1 << i) - 1)) | ((m >> (i + 1)) << i)];
                     const C A = a[g][m], Bv = a[g][p];
-                    a[g][m] = rot_update<R, false, false>(A, Bv, t, R(1));
-                    a[g][p] = rot_update<R, false, false>(Bv, A, t, R(1));
+                    a[g][m] = rot_update<R, false, false>(A, Bv, tq, R(1));
+                    a[g][p] = rot_update<R, false, false>(Bv, A, tq, R(1));
                 }
             }
         }
@@ -221,7 +256,10 @@ __global__ void __launch_bounds__(kTileThreads, tile_min_blocks<R, G, NG>()) k_t
         const TileRotP &rp = P.rot[r];
         const int mu = rp.meta & 31;
         const int m = mu ? (int)insert_zero((uint64_t)i, 31 - __clz(mu)) : i;
-        srec[r].coef[i] = (m < 32) ? xsign((R)rp.base, ((rp.smask >> m) & 1u) << 31) : R(0);
+        // coefficient of pair base (or amplitude) i, signed by parity(U(m) & zt)
+        // and by this coset's parity(k0 & z), so a thread only adds parity(j0 & zt)
+        const uint32_t sgn = ((rp.smask >> m) ^ (uint32_t)__popcll(k0 & rp.z)) & 1u;
+        srec[r].coef[i] = (m < 32) ? xsign((R)rp.base, sgn << 31) : R(0);
         if (i == 0) {
             srec[r].zt = rp.zt;
             srec[r].c = (R)rp.c;
@@ -242,6 +280,8 @@ __global__ void __launch_bounds__(kTileThreads, tile_min_blocks<R, G, NG>()) k_t
     };
     const bool do_scale = kdelta != R(0);
     const int nbatch = (1 << (B - G)) / (NG * T);
+    // amplitude indices fit 32 bits: one XOR and one wide multiply-add per store
+    const bool idx32 = (uint64_t)gridDim.x << B <= (1ull << 32);
     for (int si = 0; si < nsub; ++si) {
         const bool last = si == nsub - 1;
         const TileSubP &sp = P.sub[si];
@@ -253,44 +293,55 @@ __global__ void __launch_bounds__(kTileThreads, tile_min_blocks<R, G, NG>()) k_t
             piv[i] = sp.piv[i];
         }
         const int r0 = sp.r0, r1 = sp.r1;
-        for (int bt = 0; bt < nbatch; ++bt) {
+        // One batch of NG register groups: load from the tile, rotate, store.
+        // A full standard round (K = G rotations, the common case) gets its
+        // own copy of the whole body so its registers never meet the general
+        // path's at a join; every other round runs the per-rotation dispatch.
+        // Coset representatives: zero bits inserted at the round's pivots.  The
+        // insertion is linear over XOR and q = tid | (group << lgT) splits into
+        // disjoint fields, so j0 = spread(tid) ^ spread(group << lgT).
+        auto spread = [&](uint32_t q) {
+#pragma unroll
+            for (int i = 0; i < G; ++i) q = ((q >> piv[i]) << (piv[i] + 1)) | (q & ((1u << piv[i]) - 1));
+            return q;
+        };
+        const uint32_t j_tid = spread((uint32_t)tid);
+        // byte offsets of the group basis in the tile (shared) and in HBM (last round)
+        uint32_t ubb[G];
+#pragma unroll
+        for (int i = 0; i < G; ++i) ubb[i] = ub[i] << LS;
+        // One batch of NG register groups: load from the tile, rotate, store.
+        // A full standard round (K = G rotations, the common case) gets its
+        // own copy of the whole body so its registers never meet the general
+        // path's at a join; every other round runs the per-rotation dispatch.
+        auto batch = [&](int bt, auto mode) {
+            constexpr int K = decltype(mode)::value;
             uint32_t j0[NG];
 #pragma unroll
-            for (int g = 0; g < NG; ++g) {
-                uint32_t q = (uint32_t)(tid + (bt * NG + g) * T);
-#pragma unroll
-                for (int i = 0; i < G; ++i) q = ((q >> piv[i]) << (piv[i] + 1)) | (q & ((1u << piv[i]) - 1));
-                j0[g] = q;
-            }
+            for (int g = 0; g < NG; ++g) j0[g] = j_tid ^ spread((uint32_t)(bt * NG + g) << lgT);
             C a[NG][1 << G];
 #pragma unroll
             for (int g = 0; g < NG; ++g) {
-                uint32_t ti = j0[g];
-                a[g][0] = tile[ti];
+                uint32_t tb = j0[g] << LS;
+                a[g][0] = *reinterpret_cast<const C *>(smem + tb);
 #pragma unroll
                 for (int i = 1; i < (1 << G); ++i) {
-                    ti ^= ub[ctz_const(i)];
-                    a[g][i ^ (i >> 1)] = tile[ti];
+                    tb ^= ubb[ctz_const(i)];
+                    a[g][i ^ (i >> 1)] = *reinterpret_cast<const C *>(smem + tb);
                 }
             }
-            switch (sp.fast) {
-            case 1: fast_round<R, G, NG, 1>(a, srec + r0, j0, k0); break;
-            case 2: if constexpr (G >= 2) fast_round<R, G, NG, 2>(a, srec + r0, j0, k0); break;
-            case 3: if constexpr (G >= 3) fast_round<R, G, NG, 3>(a, srec + r0, j0, k0); break;
-            case 4: if constexpr (G >= 4) fast_round<R, G, NG, 4>(a, srec + r0, j0, k0); break;
-            case 5: if constexpr (G >= 5) fast_round<R, G, NG, 5>(a, srec + r0, j0, k0); break;
-            default:
+            if constexpr (K > 0) {
+                fast_round<R, G, NG, K>(a, srec + r0, j0);
+            } else {
                 for (int r = r0; r < r1; ++r) {
                     const KRot<R> &kr = srec[r];
                     const uint32_t meta = kr.meta;
                     const uint32_t zt = kr.zt;
-                    const uint32_t tpar = (uint32_t)__popcll(k0 & kr.z);
                     uint32_t sw[NG];
 #pragma unroll
-                    for (int g = 0; g < NG; ++g) sw[g] = ((__popc(j0[g] & zt) ^ tpar) & 1u) << 31;
+                    for (int g = 0; g < NG; ++g) sw[g] = (uint32_t)__popc(j0[g] & zt) << 31;
                     rot_dispatch<R, G, NG>((int)(meta & 127u), a, kr, sw);
                 }
-                break;
             }
             if (last) {
                 if (do_scale) {
@@ -302,31 +353,54 @@ __global__ void __launch_bounds__(kTileThreads, tile_min_blocks<R, G, NG>()) k_t
                             a[g][m].y = fma(kdelta, a[g][m].y, a[g][m].y);
                         }
                 }
-                uint64_t wb[G];
+                if (idx32) {
+                    uint32_t wb[G];
 #pragma unroll
-                for (int i = 0; i < G; ++i) wb[i] = sub_w[si][i];
+                    for (int i = 0; i < G; ++i) wb[i] = (uint32_t)sub_w[si][i];
 #pragma unroll
-                for (int g = 0; g < NG; ++g) {
-                    uint64_t gi = k0 ^ vof(j0[g] >> c) ^ ((uint64_t)j0[g] & cmask);
-                    psi[gi] = a[g][0];
+                    for (int g = 0; g < NG; ++g) {
+                        uint32_t gi = (uint32_t)(k0 ^ vof(j0[g] >> c)) ^ (j0[g] & (uint32_t)cmask);
+                        psi[gi] = a[g][0];
 #pragma unroll
-                    for (int i = 1; i < (1 << G); ++i) {
-                        gi ^= wb[ctz_const(i)];
-                        psi[gi] = a[g][i ^ (i >> 1)];
+                        for (int i = 1; i < (1 << G); ++i) {
+                            gi ^= wb[ctz_const(i)];
+                            psi[gi] = a[g][i ^ (i >> 1)];
+                        }
+                    }
+                } else {
+                    uint64_t wb[G];
+#pragma unroll
+                    for (int i = 0; i < G; ++i) wb[i] = sub_w[si][i];
+#pragma unroll
+                    for (int g = 0; g < NG; ++g) {
+                        uint64_t gi = k0 ^ vof(j0[g] >> c) ^ ((uint64_t)j0[g] & cmask);
+                        psi[gi] = a[g][0];
+#pragma unroll
+                        for (int i = 1; i < (1 << G); ++i) {
+                            gi ^= wb[ctz_const(i)];
+                            psi[gi] = a[g][i ^ (i >> 1)];
+                        }
                     }
                 }
             } else {
 #pragma unroll
                 for (int g = 0; g < NG; ++g) {
-                    uint32_t ti = j0[g];
-                    tile[ti] = a[g][0];
+                    uint32_t tb = j0[g] << LS;
+                    *reinterpret_cast<C *>(smem + tb) = a[g][0];
 #pragma unroll
                     for (int i = 1; i < (1 << G); ++i) {
-                        ti ^= ub[ctz_const(i)];
-                        tile[ti] = a[g][i ^ (i >> 1)];
+                        tb ^= ubb[ctz_const(i)];
+                        *reinterpret_cast<C *>(smem + tb) = a[g][i ^ (i >> 1)];
                     }
                 }
             }
+        };
+        const bool full = sp.fast == G;
+        for (int bt = 0; bt < nbatch; ++bt) {
+            if (full)
+                batch(bt, std::integral_constant<int, G>{});
+            else
+                batch(bt, std::integral_constant<int, 0>{});
         }
         if (!last) __syncthreads();
     }
