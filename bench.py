@@ -135,14 +135,21 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def tile_kernel_sha256():
+    """Hash of the tile kernel's device sources (the pass body and its launch)."""
+    h = hashlib.sha256()
+    for f in ("ps_device.cuh", "ps_tile.cuh", "ps_tile.cu"):
+        h.update(open(os.path.join(ROOT, "paper_2504_17881_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()
+
+
 def kernel_traffic():
     """Per-launch DRAM bytes of the tile kernel from the committed ncu summary, if the
     kernel source is unchanged since it was taken."""
     path = os.path.join(ROOT, "profiles", "k_tile_c64_n30.txt")
-    src = os.path.join(ROOT, "paper_2504_17881_gb300", "csrc", "ps_tile.cu")
     try:
         text = open(path).read()
-        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+        sha = tile_kernel_sha256()
     except OSError:
         return None
     fields = dict(ln.split(":", 1) for ln in text.splitlines() if ":" in ln and not ln.startswith(" "))

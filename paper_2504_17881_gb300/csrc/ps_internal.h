@@ -137,6 +137,52 @@ struct PairParams {
     uint32_t pad;
 };
 
+// ------------------------------------------------------------ batched runs
+// Many independent runs in one persistent, cooperative launch.  Runs with
+// n <= lane_min_n - 1 are taken one per CTA from an atomic queue (longest
+// first); larger runs go to lanes of co-resident CTAs that split every
+// window's tiles and meet at a bounded-wait barrier between windows.
+
+struct BatchRun {
+    int32_t n;
+    int32_t lane;        // -1: single-CTA queue
+    uint32_t win_off;    // first window in the batch's window table
+    uint32_t nwin;
+};
+
+struct BatchWin {
+    uint64_t body;       // byte offset of the packed window (head, rounds, rotations)
+    double kdelta;       // stored-scale correction applied by this pass
+    int32_t B;           // tile bits (c + d)
+    int32_t pad;
+};
+
+// Packed window head: the leading part of TileParams (v, piv, c, d, nsub, nrot).
+constexpr size_t kWinHeadBytes = offsetof(TileParams, sub);
+
+struct BatchArgs {
+    const BatchRun *runs;
+    const BatchWin *wins;
+    const unsigned char *bodies;
+    void *const *states;        // per run: device state
+    const void *const *psi0;    // per run: device reference state (may be null: no overlap)
+    double *overlaps;           // per run: re, im
+    double *partials;           // per lane member: re, im
+    unsigned *lane_ctr;         // per lane: arrivals
+    unsigned *lane_gen;         // per lane: barrier generation
+    const int *lane_runs;       // runs of each lane, lane by lane
+    const int *lane_off;        // nlanes + 1 offsets into lane_runs
+    const int *single_order;    // queue order of single-CTA runs
+    unsigned *queue;            // next queue slot
+    int *status;                // PS_OK, or PS_ERR_TIMEOUT once a wait ran out
+    int nlanes, lane_size, nsingle;
+    int withhold;               // test hook: lane member lane_size-1 never arrives at barriers
+    long long budget_ns;        // bound of every device-side wait
+};
+
+int launch_batch(int dtype, int G, int NG, const BatchArgs &a, int grid, void *stream, int capture_safe);
+int batch_grid(int dtype, int G, int NG, int num_sms, int *grid_out);
+
 // After its rotations a pass applies a <- a + kdelta * a to every amplitude:
 // the part of the accumulated cos(phi) factors the state stores.
 int launch_tile(int dtype, int G, int ng_request, void *psi, int n, const TileParams &tp, double kdelta,
