@@ -268,6 +268,99 @@ int ps_evolve_partial(ps_state *st, const ps_ham *ham, size_t L_D, double t, uin
 int ps_get_stats(ps_state *st, ps_stats *out);
 int ps_reset_stats(ps_state *st);
 
+/* --------------------------------------------------------------- batches
+ *
+ * Many independent runs in one persistent launch.  The paper runs its
+ * independent simulations -- other Hamiltonians, times, step counts and
+ * random samples -- as separate jobs, hundreds at a time (Methods,
+ * "Computational details"); here they share one cooperative kernel,
+ * replayed from a CUDA graph:
+ *   - runs with n <= resident_bits keep their whole state in one CTA's
+ *     shared memory for all their windows;
+ *   - other runs with n <= single_bits run on one CTA, tile by tile;
+ *   - larger runs go to lanes of lane_size co-resident CTAs that split each
+ *     window's tiles and meet at a bounded-wait barrier before the next;
+ *   - lanes get their runs longest first (work 2^n x windows) on the host,
+ *     and every CTA that has finished its lane takes single runs from a
+ *     device queue, longest first.
+ * Every run starts from psi0 (read-only; the state is written by the first
+ * window), so a replay recomputes the same result, and ends with the FP64
+ * overlap <psi0|psi> summed in a fixed order.  The evolved state is stored
+ * exactly (no pending cos(phi) scale: the last window applies all of it).
+ * A device-side wait that runs out (wait_ms) makes the launch return
+ * PS_ERR_TIMEOUT from ps_batch_wait; the states are then undefined.
+ */
+typedef struct ps_batch ps_batch; /* opaque: scheduled runs resident on one device */
+
+typedef struct ps_run_desc {
+    int n;             /* qubits, 4..30 */
+    void *state;       /* device buffer of 2^n amplitudes of the batch dtype, 16-byte aligned; receives
+                          the evolved state.  Runs never share a state buffer. */
+    const void *psi0;  /* device initial state (read only; runs may share one), or NULL: the run evolves
+                          `state` in place, a replay continues from where the last one ended, and the
+                          overlap reported is 0 */
+    const uint64_t *x; /* host arrays of `count` rotations in application order, copied at creation */
+    const uint64_t *z;
+    const double *phi;
+    size_t count;
+} ps_run_desc;
+
+/* Zero in any field selects the default. */
+typedef struct ps_batch_config {
+    int lane_size;     /* CTAs per lane: a power of two, 1..256 (default 16) */
+    int tile_bits;     /* largest tile of a lane or single run, 8..13 for PS_C64 and 8..12 for PS_C128
+                          (default 13 / 12); a lane run of n qubits uses
+                          min(tile_bits, max(8, n - log2(lane_size))) */
+    int resident_bits; /* runs with n <= resident_bits are resident in shared memory; at most 13 (PS_C64)
+                          / 12 (PS_C128), the default; -1: none */
+    int single_bits;   /* runs with n <= single_bits (and not resident) run on one CTA; -1: none;
+                          default resident_bits + 1 */
+    int use_graph;     /* default / 1: capture the launch in a CUDA graph; -1: plain launches */
+    int wait_ms;       /* bound of every device-side wait, milliseconds (default 5000) */
+    int test_withhold; /* test hook: 1 makes the last CTA of lane 0 skip its barrier arrivals, so the
+                          lane's waits run out and ps_batch_wait returns PS_ERR_TIMEOUT */
+} ps_batch_config;
+
+typedef struct ps_batch_info {
+    uint64_t runs, lane_runs, single_runs, resident_runs;
+    uint64_t rotations;         /* summed over runs */
+    uint64_t windows;           /* tile passes summed over runs */
+    double amplitude_passes;    /* sum over runs of 2^n x windows */
+    double amplitude_rotations; /* sum over runs of 2^n x rotations */
+    uint64_t body_bytes;        /* device bytes of the packed windows */
+    uint64_t smem_bytes;        /* dynamic shared memory per CTA */
+    double max_lane_work;       /* largest lane's sum of 2^n x (windows + 1) */
+    double single_work;         /* the same summed over single runs */
+    int grid, ctas_per_sm, lanes, lane_size, tile_bits, resident_bits, single_bits, graph;
+} ps_batch_info;
+
+/* Schedule every run (host, in parallel threads), upload the windows and
+ * prepare the launch on `stream` (a cudaStream_t; the current device).
+ * Fails with PS_ERR_ARG on an invalid run (n outside 4..30, null or
+ * misaligned buffers, a state shared by two runs or aliasing a psi0, a mask
+ * bit >= n, a non-finite angle) or configuration, PS_ERR_OOM when device
+ * memory runs out, PS_ERR_CUDA when the cooperative launch cannot hold the
+ * grid. */
+int ps_batch_create(int dtype, const ps_run_desc *runs, size_t nruns, const ps_batch_config *cfg, void *stream,
+                    ps_batch **out);
+/* Start all runs (asynchronous on the batch's stream). */
+int ps_batch_launch(ps_batch *b);
+/* Wait for the last launch; copy 2*nruns doubles (re, im of <psi0|psi> per
+ * run) to `overlaps` unless it is NULL.  PS_ERR_TIMEOUT if a wait ran out. */
+int ps_batch_wait(ps_batch *b, double *overlaps);
+/* ps_batch_launch then ps_batch_wait. */
+int ps_batch_run(ps_batch *b, double *overlaps);
+int ps_batch_get_info(const ps_batch *b, ps_batch_info *out);
+void ps_batch_destroy(ps_batch *b);
+
+/* Host-only dry run of ps_batch_create for an assumed grid (ctas_per_sm x
+ * num_sms CTAs): the schedule without device work.  state and psi0 may be
+ * NULL.  Per run, lane_of receives the lane (>= 0), -1 (single CTA) or -2
+ * (resident), tile_bits_of the tile bits and windows_of the windows; any of
+ * the three may be NULL. */
+int ps_batch_describe(int dtype, const ps_run_desc *runs, size_t nruns, const ps_batch_config *cfg, int num_sms,
+                      int ctas_per_sm, ps_batch_info *out, int *lane_of, int *tile_bits_of, uint64_t *windows_of);
+
 #ifdef __cplusplus
 }
 #endif

@@ -11,15 +11,16 @@ memory and streams.
 from __future__ import annotations
 
 from . import _lib
-from ._lib import (PS_C64, PS_C128, PsError, ps_abi_version, ps_apply_rotations, ps_copy_state, ps_create,  # noqa: F401
+from ._lib import (PS_C64, PS_C128, PS_ERR_ARG, PS_ERR_TIMEOUT, PsError, ps_abi_version, ps_apply_rotations, ps_copy_state, ps_create,  # noqa: F401
                    ps_destroy, ps_device_count, ps_evolve_partial, ps_evolve_qdrift, ps_evolve_trotter,
                    ps_get_scale, ps_get_state, ps_get_stats, ps_ham_create, ps_ham_destroy, ps_ham_lambda, ps_last_error, ps_norm,
                    ps_overlap, ps_overlap_noalloc, ps_partial_length, ps_partial_stream, ps_plan_apply, ps_plan_create, ps_plan_describe,
                    ps_plan_destroy, ps_plan_export, ps_plan_get_info, ps_qdrift_stream, ps_reset_stats,
-                   ps_set_state, ps_set_tuning)
+                   ps_set_state, ps_set_tuning, ps_batch_create, ps_batch_launch, ps_batch_wait, ps_batch_run,
+                   ps_batch_get_info, ps_batch_destroy, ps_batch_describe)
 
-__all__ = [n for n in dir(_lib) if n.startswith("ps_")] + ["StateVector", "Hamiltonian", "Plan", "PsError",
-                                                              "PS_C64", "PS_C128"]
+__all__ = [n for n in dir(_lib) if n.startswith("ps_")] + ["StateVector", "Hamiltonian", "Plan", "Batch",
+                                                              "PsError", "PS_C64", "PS_C128"]
 
 
 def _torch():
@@ -151,6 +152,56 @@ class Plan:
     def close(self):
         if getattr(self, "handle", None):
             ps_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Independent runs in one persistent launch (libps batches).
+
+    runs: sequence of dicts with n, x, z, phi and optionally psi0 (a CUDA
+    tensor, the initial state; shared by runs or not).  Every run gets its own
+    output state tensor (``states[i]``); a run without psi0 evolves its state
+    tensor in place (fill it before launching).
+    """
+
+    def __init__(self, runs, dtype=None, cfg=None, device=None, stream=None):
+        torch = _torch()
+        dtype = torch.complex64 if dtype is None else dtype
+        self.ps_dtype = _ps_dtype(dtype)
+        dev = device or "cuda"
+        self.states = [r.get("state") if r.get("state") is not None else
+                       torch.zeros(1 << int(r["n"]), dtype=dtype, device=dev) for r in runs]
+        self.psi0 = [r.get("psi0") for r in runs]
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.states[0].device)
+        descs = []
+        for r, st, p0 in zip(runs, self.states, self.psi0):
+            if st.dtype != dtype or (p0 is not None and p0.dtype != dtype):
+                raise ValueError("every state and psi0 must have the batch dtype")
+            descs.append(dict(n=int(r["n"]), state=st.data_ptr(), psi0=p0.data_ptr() if p0 is not None else 0,
+                              x=r["x"], z=r["z"], phi=r["phi"]))
+        self.nruns = len(descs)
+        self.handle = ps_batch_create(self.ps_dtype, descs, cfg, self.stream.cuda_stream)
+        self.info = ps_batch_get_info(self.handle)
+
+    def launch(self):
+        ps_batch_launch(self.handle)
+
+    def wait(self):
+        return ps_batch_wait(self.handle, self.nruns)
+
+    def run(self):
+        """Launch, wait, and return <psi0|psi> per run (complex128 numpy array)."""
+        return ps_batch_run(self.handle, self.nruns)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            ps_batch_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

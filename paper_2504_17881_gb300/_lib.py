@@ -44,6 +44,27 @@ class ps_plan_info(ctypes.Structure):
                 ("tile_bits", ctypes.c_int), ("group_bits", ctypes.c_int)]
 
 
+class ps_run_desc(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int), ("state", ctypes.c_void_p), ("psi0", ctypes.c_void_p),
+                ("x", ctypes.c_void_p), ("z", ctypes.c_void_p), ("phi", ctypes.c_void_p), ("count", ctypes.c_size_t)]
+
+
+class ps_batch_config(ctypes.Structure):
+    _fields_ = [("lane_size", ctypes.c_int), ("tile_bits", ctypes.c_int), ("resident_bits", ctypes.c_int),
+                ("single_bits", ctypes.c_int), ("use_graph", ctypes.c_int), ("wait_ms", ctypes.c_int),
+                ("test_withhold", ctypes.c_int)]
+
+
+class ps_batch_info(ctypes.Structure):
+    _fields_ = [("runs", ctypes.c_uint64), ("lane_runs", ctypes.c_uint64), ("single_runs", ctypes.c_uint64),
+                ("resident_runs", ctypes.c_uint64), ("rotations", ctypes.c_uint64), ("windows", ctypes.c_uint64),
+                ("amplitude_passes", ctypes.c_double), ("amplitude_rotations", ctypes.c_double),
+                ("body_bytes", ctypes.c_uint64), ("smem_bytes", ctypes.c_uint64), ("max_lane_work", ctypes.c_double),
+                ("single_work", ctypes.c_double), ("grid", ctypes.c_int), ("ctas_per_sm", ctypes.c_int),
+                ("lanes", ctypes.c_int), ("lane_size", ctypes.c_int), ("tile_bits", ctypes.c_int),
+                ("resident_bits", ctypes.c_int), ("single_bits", ctypes.c_int), ("graph", ctypes.c_int)]
+
+
 if not os.path.exists(LIB_PATH):
     raise ImportError(f"{LIB_PATH} is not built: run `python -m paper_2504_17881_gb300.build` "
                       "(or __graft_entry__.build()); there is no non-CUDA fallback")
@@ -85,6 +106,14 @@ _SIGS = {
     "ps_evolve_partial": (_i, [_vp, _vp, _sz, _d, _u32, _u64, _u64]),
     "ps_get_stats": (_i, [_vp, ctypes.POINTER(ps_stats)]),
     "ps_reset_stats": (_i, [_vp]),
+    "ps_batch_create": (_i, [_i, ctypes.POINTER(ps_run_desc), _sz, ctypes.POINTER(ps_batch_config), _vp, _pp]),
+    "ps_batch_launch": (_i, [_vp]),
+    "ps_batch_wait": (_i, [_vp, _vp]),
+    "ps_batch_run": (_i, [_vp, _vp]),
+    "ps_batch_get_info": (_i, [_vp, ctypes.POINTER(ps_batch_info)]),
+    "ps_batch_destroy": (None, [_vp]),
+    "ps_batch_describe": (_i, [_i, ctypes.POINTER(ps_run_desc), _sz, ctypes.POINTER(ps_batch_config), _i, _i,
+                               ctypes.POINTER(ps_batch_info), _vp, _vp, _vp]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _fn = getattr(lib, _name)
@@ -305,3 +334,89 @@ def ps_get_stats(h: int) -> dict:
 
 def ps_reset_stats(h: int):
     _check(lib.ps_reset_stats(ctypes.c_void_p(h)))
+
+
+# ----------------------------------------------------------------- batches
+
+def _batch_config(cfg) -> ps_batch_config | None:
+    if cfg is None:
+        return None
+    if isinstance(cfg, ps_batch_config):
+        return cfg
+    return ps_batch_config(**{k: int(v) for k, v in dict(cfg).items()})
+
+
+def _run_descs(runs):
+    """runs: sequence of dicts n, state (device pointer or 0), psi0 (pointer or 0/None), x, z, phi.
+    Returns the ctypes array and the numpy arrays it points into (kept alive by the caller)."""
+    keep = []
+    arr = (ps_run_desc * len(runs))()
+    for i, r in enumerate(runs):
+        x, z, phi = _u64a(r["x"]), _u64a(r["z"]), _f64a(r["phi"])
+        if not (len(x) == len(z) == len(phi)):
+            raise ValueError("x, z and phi differ in length")
+        keep += [x, z, phi]
+        arr[i] = ps_run_desc(int(r["n"]), r.get("state") or None, r.get("psi0") or None,
+                             x.ctypes.data if len(x) else None, z.ctypes.data if len(z) else None,
+                             phi.ctypes.data if len(phi) else None, len(x))
+    return arr, keep
+
+
+def _batch_info_dict(info: ps_batch_info) -> dict:
+    return {k: getattr(info, k) for k, _ in ps_batch_info._fields_}
+
+
+def ps_batch_create(dtype: int, runs, cfg=None, stream: int | None = None) -> int:
+    arr, keep = _run_descs(runs)
+    h = ctypes.c_void_p()
+    c = _batch_config(cfg)
+    _check(lib.ps_batch_create(dtype, arr, len(runs), ctypes.byref(c) if c is not None else None,
+                               ctypes.c_void_p(stream or 0), ctypes.byref(h)))
+    del keep
+    return h.value
+
+
+def ps_batch_launch(b: int):
+    _check(lib.ps_batch_launch(ctypes.c_void_p(b)))
+
+
+def ps_batch_wait(b: int, nruns: int | None = None):
+    """Wait; returns the overlaps as a complex128 array when nruns is given."""
+    if nruns is None:
+        _check(lib.ps_batch_wait(ctypes.c_void_p(b), None))
+        return None
+    out = np.zeros(2 * nruns, dtype=np.float64)
+    _check(lib.ps_batch_wait(ctypes.c_void_p(b), _ptr(out)))
+    return out[0::2] + 1j * out[1::2]
+
+
+def ps_batch_run(b: int, nruns: int):
+    out = np.zeros(2 * nruns, dtype=np.float64)
+    _check(lib.ps_batch_run(ctypes.c_void_p(b), _ptr(out)))
+    return out[0::2] + 1j * out[1::2]
+
+
+def ps_batch_get_info(b: int) -> dict:
+    info = ps_batch_info()
+    _check(lib.ps_batch_get_info(ctypes.c_void_p(b), ctypes.byref(info)))
+    return _batch_info_dict(info)
+
+
+def ps_batch_destroy(b: int):
+    lib.ps_batch_destroy(ctypes.c_void_p(b))
+
+
+def ps_batch_describe(dtype: int, runs, cfg=None, num_sms: int = 152, ctas_per_sm: int = 3) -> dict:
+    """Host-only schedule of a batch (no GPU): info plus per-run lane, tile bits and windows."""
+    arr, keep = _run_descs(runs)
+    info = ps_batch_info()
+    lane = np.zeros(len(runs), dtype=np.int32)
+    tb = np.zeros(len(runs), dtype=np.int32)
+    nw = np.zeros(len(runs), dtype=np.uint64)
+    c = _batch_config(cfg)
+    _check(lib.ps_batch_describe(dtype, arr, len(runs), ctypes.byref(c) if c is not None else None, num_sms,
+                                 ctas_per_sm, ctypes.byref(info), _ptr(lane), _ptr(tb), _ptr(nw)))
+    del keep
+    d = _batch_info_dict(info)
+    d.update(lane_of=lane, tile_bits_of=tb, windows_of=nw)
+    return d

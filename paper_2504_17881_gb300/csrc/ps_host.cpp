@@ -37,7 +37,7 @@ static int cuda_fail(cudaError_t e, const char *what) {
     } while (0)
 
 // Kernel parameters of one window, read from the host copy of the plan.
-static void fill_tile_params(const Plan &p, const WinDesc &w, TileParams &tp) {
+void fill_tile_params(const Plan &p, const WinDesc &w, TileParams &tp) {
     std::memset(&tp, 0, sizeof(tp));
     for (int i = 0; i < w.d; ++i) {
         tp.v[i] = w.v[i];

@@ -138,23 +138,20 @@ struct PairParams {
 };
 
 // ------------------------------------------------------------ batched runs
-// Many independent runs in one persistent, cooperative launch.  Runs with
-// n <= lane_min_n - 1 are taken one per CTA from an atomic queue (longest
-// first); larger runs go to lanes of co-resident CTAs that split every
-// window's tiles and meet at a bounded-wait barrier between windows.
+// Many independent runs in one persistent, cooperative launch (ps_batch.cu).
 
 struct BatchRun {
     int32_t n;
-    int32_t lane;        // -1: single-CTA queue
+    int32_t lane;        // >= 0: lane index; -1: single CTA; -2: single CTA, state resident in shared memory
     uint32_t win_off;    // first window in the batch's window table
     uint32_t nwin;
 };
 
 struct BatchWin {
-    uint64_t body;       // byte offset of the packed window (head, rounds, rotations)
-    double kdelta;       // stored-scale correction applied by this pass
-    int32_t B;           // tile bits (c + d)
-    int32_t pad;
+    uint64_t body;       // byte offset of the packed window: head, rounds (padded to 8 bytes), rotations
+    double kdelta;       // a <- a + kdelta a after the window's rotations
+    int32_t B;           // tile bits c + d
+    int16_t nsub, nrot;
 };
 
 // Packed window head: the leading part of TileParams (v, piv, c, d, nsub, nrot).
@@ -164,24 +161,35 @@ struct BatchArgs {
     const BatchRun *runs;
     const BatchWin *wins;
     const unsigned char *bodies;
-    void *const *states;        // per run: device state
-    const void *const *psi0;    // per run: device reference state (may be null: no overlap)
+    void *const *states;        // per run: device state (written)
+    const void *const *psi0;    // per run: device initial state, or null (evolve the state in place, no overlap)
     double *overlaps;           // per run: re, im
-    double *partials;           // per lane member: re, im
-    unsigned *lane_ctr;         // per lane: arrivals
-    unsigned *lane_gen;         // per lane: barrier generation
+    double *partials;           // two buffers of one (re, im) per lane member
+    unsigned *lane_ctr;         // per lane (stride 32 words): arrivals
+    unsigned *lane_gen;         // per lane (stride 32 words): barrier generation
     const int *lane_runs;       // runs of each lane, lane by lane
     const int *lane_off;        // nlanes + 1 offsets into lane_runs
-    const int *single_order;    // queue order of single-CTA runs
+    const int *single_order;    // queue order of the single-CTA runs
     unsigned *queue;            // next queue slot
     int *status;                // PS_OK, or PS_ERR_TIMEOUT once a wait ran out
     int nlanes, lane_size, nsingle;
-    int withhold;               // test hook: lane member lane_size-1 never arrives at barriers
+    int withhold;               // test hook: the last member of lane 0 never arrives at a barrier
     long long budget_ns;        // bound of every device-side wait
 };
 
-int launch_batch(int dtype, int G, int NG, const BatchArgs &a, int grid, void *stream, int capture_safe);
-int batch_grid(int dtype, int G, int NG, int num_sms, int *grid_out);
+// Resident CTAs per SM of the batched kernel with this dynamic shared memory
+// (also raises the kernel's dynamic shared-memory limit to it).
+int batch_occupancy(int dtype, size_t smem_bytes, int *blocks_per_sm);
+// Cooperative launch of the batched kernel (kTileThreads threads per CTA).
+int launch_batch(int dtype, const BatchArgs &a, int grid, size_t smem_bytes, void *stream);
+constexpr int kBatchThreads = 256;
+// Bytes of one per-rotation record in a tile pass's shared memory (KRot).
+constexpr size_t kRecBytesC64 = 160, kRecBytesC128 = 288;
+constexpr int kBatchG = 3;       // group bits of the batched kernel
+constexpr int kLaneStrideWords = 32;
+
+// Kernel parameters of one tile window, from the host copy of a plan.
+void fill_tile_params(const Plan &p, const WinDesc &w, TileParams &tp);
 
 // After its rotations a pass applies a <- a + kdelta * a to every amplitude:
 // the part of the accumulated cos(phi) factors the state stores.

@@ -6,7 +6,7 @@ namespace ps {
 template <typename R, int G, int NG>
 __global__ void __launch_bounds__(kTileThreads, tile_min_blocks<R, G, NG>()) k_tile(typename CT<R>::T *__restrict__ psi,
                                                           const __grid_constant__ TileParams P, int n, R kdelta) {
-    tile_pass<R, G, NG>(psi, P, blockIdx.x, n, kdelta);
+    tile_pass<R, G, NG, false>(psi, psi, P, blockIdx.x, n, kdelta, true, true);
 }
 
 // ------------------------------------------------------------------ launch

@@ -41,6 +41,9 @@ template <> struct __align__(16) KRot<double> {
     double c, pad;
 };
 
+static_assert(sizeof(KRot<float>) == kRecBytesC64 && sizeof(KRot<double>) == kRecBytesC128,
+              "record sizes used by the host launchers");
+
 // One rotation on the NG register groups of a thread, each of 2^G
 // amplitudes a[g][m] (tile index j0_g ^ U(m)).  MU: the rotation's X mask in
 // group coordinates (the partner of a[g][m] is a[g][m ^ MU]).  sw[g]: sign
@@ -93,9 +96,6 @@ __device__ __forceinline__ void rot_dispatch(int code, typename CT<R>::T (&a)[NG
 #undef PS_C8
 #undef PS_C1
 
-// Standard round: K tangent-form rotations with an even number of Y factors
-// whose group X masks are 1, 2, ..., 2^(K-1) in order, as straight-line code
-// (no per-rotation dispatch), so registers are renamed freely between updates.
 // Coefficients 0..NC-1 of a record, read as 16-byte vectors.
 template <typename R, int NC>
 __device__ __forceinline__ void load_coefs(const KRot<R> &k, R (&cf)[NC]) {
@@ -196,12 +196,24 @@ constexpr int tile_min_blocks() {
     return (NG << G) * (int)sizeof(R) <= 64 ? 3 : 2;
 }
 
-// One tile pass: coset H of the window P (n-qubit state).  Used by k_tile
-// (one tile per CTA) and by the batched kernel (many tiles per CTA); the
-// leading barrier keeps a CTA's consecutive passes from overlapping.
-template <typename R, int G, int NG>
-__device__ __forceinline__ void tile_pass(typename CT<R>::T *__restrict__ psi, const TileParams &P, uint32_t H,
-                                          int n, R kdelta) {
+// One tile pass: coset H of the window P (n-qubit state), read from src and
+// written to dst (the same buffer for an in-place pass).  Used by k_tile (one
+// tile per CTA) and by the batched kernel (many tiles per CTA); the leading
+// barrier keeps a CTA's consecutive passes from overlapping.
+//   load:         stage the tile from src; otherwise it is already in shared
+//                 memory (a run whose whole state stays on chip: c = n, d = 0);
+//   store_global: the last round writes to dst; otherwise back to the tile.
+// GEN = false (the single-window kernel): load and store_global are true and
+// the block has exactly one thread per NG register groups, at most.  GEN =
+// true (the batched kernel): the flags are honoured and the block may hold
+// more threads than the tile has register groups; the surplus threads then
+// only help with the copies and tables.
+template <typename R, int G, int NG, bool GEN>
+__device__ __forceinline__ void tile_pass(const typename CT<R>::T *src, typename CT<R>::T *__restrict__ psi,
+                                          const TileParams &P, uint32_t H, int n, R kdelta, bool load_,
+                                          bool store_global_) {
+    const bool load = GEN ? load_ : true;
+    const bool store_global = GEN ? store_global_ : true;
     using C = typename CT<R>::T;
     constexpr int LS = sizeof(C) == 8 ? 3 : 4;  // log2 bytes per amplitude
     extern __shared__ __align__(16) unsigned char smem[];
@@ -212,8 +224,10 @@ __device__ __forceinline__ void tile_pass(typename CT<R>::T *__restrict__ psi, c
     const int B = c + d;
     const int nsub = P.nsub, nrot = P.nrot;
     const int tid = threadIdx.x;
-    const int T = blockDim.x;
-    const int lgT = 31 - __clz(T);
+    const int lgB = 31 - __clz(blockDim.x);
+    // threads of the register rounds: at most one per NG groups
+    const int lgT = GEN ? min(lgB, B - G - (NG == 4 ? 2 : NG == 2 ? 1 : 0)) : lgB;
+    const int T = 1 << lgT;
     const uint64_t cmask = (1ull << c) - 1;
     C *tile = reinterpret_cast<C *>(smem);
     KRot<R> *srec = reinterpret_cast<KRot<R> *>(smem + ((size_t)sizeof(C) << B));
@@ -224,32 +238,33 @@ __device__ __forceinline__ void tile_pass(typename CT<R>::T *__restrict__ psi, c
         k0 = ((k0 >> p) << (p + 1)) | (k0 & ((1ull << p) - 1));
     }
 
-    // ---- issue the tile loads: chunk ch = tid + i*T (16 bytes each).  When T
-    // covers whole segments, seg = (tid >> seg_log) | (i << it_shift) and
-    // V(seg) = V(tid >> seg_log) ^ V(i << it_shift), walked in Gray order.
+    // ---- issue the tile loads: chunk ch = tid + i*blockDim (16 bytes each).
+    // When the block covers whole segments, seg = (tid >> seg_log) |
+    // (i << it_shift) and V(seg) = V(tid >> seg_log) ^ V(i << it_shift),
+    // walked in Gray order.
     const int seg_log = c + LS - 4;
-    const int niter = (1 << (B + LS - 4)) >> lgT;
-    char *gbase = reinterpret_cast<char *>(psi);
-    if (lgT >= seg_log) {
-        const int it_shift = lgT - seg_log;
+    const int lgchunks = B + LS - 4;
+    const char *gbase = reinterpret_cast<const char *>(src);
+    if (!load) {
+    } else if (lgB >= seg_log && (!GEN || lgchunks >= lgB)) {
+        const int niter = 1 << (lgchunks - lgB);
+        const int it_shift = lgB - seg_log;
         const uint64_t base = k0 ^ v_of(P, (uint32_t)tid >> seg_log);
         const uint64_t off = (uint64_t)((uint32_t)tid & ((1u << seg_log) - 1)) << 4;
         uint64_t vi = 0;
         for (int i = 0; i < niter; ++i) {
             if (i) vi ^= P.v[it_shift + (__ffs(i) - 1)];
             const int gi = i ^ (i >> 1);
-            cp_async16(smem + (size_t)(tid + (gi << lgT)) * 16, gbase + ((base ^ vi) << LS) + off);
+            cp_async16(smem + (size_t)(tid + (gi << lgB)) * 16, gbase + ((base ^ vi) << LS) + off);
         }
     } else {
-        for (int i = 0; i < niter; ++i) {
-            const uint32_t ch = (uint32_t)(tid + (i << lgT));
+        for (uint32_t ch = (uint32_t)tid; ch < (1u << lgchunks); ch += blockDim.x)
             cp_async16(smem + (size_t)ch * 16,
                        gbase + ((k0 ^ v_of(P, ch >> seg_log)) << LS) + ((uint64_t)(ch & ((1u << seg_log) - 1)) << 4));
-        }
     }
 
     // ---- per-window tables while the copies are in flight
-    for (int e = tid; e < 64; e += T) {
+    for (int e = tid; e < 64; e += blockDim.x) {
         const int k = e >> 4, jj = e & 15;
         uint64_t acc = 0;
 #pragma unroll
@@ -259,7 +274,7 @@ __device__ __forceinline__ void tile_pass(typename CT<R>::T *__restrict__ psi, c
         }
         nib[k][jj] = acc;
     }
-    for (int e = tid; e < nrot * 32; e += T) {
+    for (int e = tid; e < nrot * 32; e += blockDim.x) {
         const int r = e >> 5, i = e & 31;
         const TileRotP &rp = P.rot[r];
         const int mu = rp.meta & 31;
@@ -275,7 +290,7 @@ __device__ __forceinline__ void tile_pass(typename CT<R>::T *__restrict__ psi, c
             srec[r].meta = rp.meta;
         }
     }
-    for (int e = tid; e < nsub * G; e += T) {
+    for (int e = tid; e < nsub * G; e += blockDim.x) {
         const int si = e / G, i = e % G;
         const uint32_t u = P.sub[si].u[i];
         sub_w[si][i] = v_of(P, u >> c) ^ ((uint64_t)u & cmask);
@@ -351,8 +366,7 @@ __device__ __forceinline__ void tile_pass(typename CT<R>::T *__restrict__ psi, c
                     rot_dispatch<R, G, NG>((int)(meta & 127u), a, kr, sw);
                 }
             }
-            if (last) {
-                if (do_scale) {
+            if (last && do_scale) {
 #pragma unroll
                     for (int g = 0; g < NG; ++g)
 #pragma unroll
@@ -360,7 +374,8 @@ __device__ __forceinline__ void tile_pass(typename CT<R>::T *__restrict__ psi, c
                             a[g][m].x = fma(kdelta, a[g][m].x, a[g][m].x);
                             a[g][m].y = fma(kdelta, a[g][m].y, a[g][m].y);
                         }
-                }
+            }
+            if (last && store_global) {
                 if (idx32) {
                     uint32_t wb[G];
 #pragma unroll
@@ -404,13 +419,15 @@ __device__ __forceinline__ void tile_pass(typename CT<R>::T *__restrict__ psi, c
             }
         };
         const bool full = sp.fast == G;
-        for (int bt = 0; bt < nbatch; ++bt) {
-            if (full)
-                batch(bt, std::integral_constant<int, G>{});
-            else
-                batch(bt, std::integral_constant<int, 0>{});
+        if (!GEN || tid < T) {
+            for (int bt = 0; bt < nbatch; ++bt) {
+                if (full)
+                    batch(bt, std::integral_constant<int, G>{});
+                else
+                    batch(bt, std::integral_constant<int, 0>{});
+            }
         }
-        if (!last) __syncthreads();
+        if (!last || !store_global) __syncthreads();
     }
 }
 

@@ -64,7 +64,11 @@ def jw_hamiltonian(n: int, L: int, seed: int, lam: float | None = None, p_two_qu
     rng = np.random.default_rng(seed)
     terms: dict[tuple[int, int], float] = {}
     order: list[tuple[int, int]] = []
+    attempts = 0
     while len(order) < L:
+        attempts += 1
+        if attempts > 1000 * L + 10000:
+            raise ValueError(f"cannot draw {L} distinct JW-like terms on {n} qubits")
         w = 2 if rng.random() < p_two_qubit else 4
         q = np.sort(rng.choice(n, size=w, replace=False))
         ys = rng.integers(0, 2, size=w)
