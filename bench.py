@@ -47,6 +47,8 @@ SEG_LEN = N_SAMPLES // SEGMENTS
 FP64_PREFIX = 1000
 CPU_SAMPLE_ROTATIONS = 2
 FALLBACK_HBM_GBS = 6800.0
+BATCH_RUNS = 512
+BATCH_SEED = 5
 
 
 def workload_name():
@@ -64,6 +66,12 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--workload", choices=["qdrift30", "batched"], default="qdrift30",
+                    help="batched: 512 independent qDRIFT / partially randomised runs, n 14..22, in one "
+                         "persistent launch (reported on its own JSON line)")
+    ap.add_argument("--batch-runs", type=int, default=BATCH_RUNS)
+    ap.add_argument("--no-sequential", action="store_true", help="batched: skip the one-run-at-a-time comparison")
+    ap.add_argument("--no-autotune", action="store_true", help="batched: default lane size and tile bits")
     ap.add_argument("--qubits", type=int, default=30,
                     help="state size; values other than 30 are for profiling captures only")
     return ap.parse_args()
@@ -395,6 +403,186 @@ def cpu_baseline_leg():
             "host_cores_available": os.cpu_count()}
 
 
+# ---------------------------------------------------------------- batched
+
+def batched_workload(nruns: int, seed: int = BATCH_SEED):
+    """Independent runs of uneven size: n uniform in 14..22, 200-2000 JW-like
+    terms per Hamiltonian, 2000-20000 rotations; even runs qDRIFT, odd runs
+    partially randomised (L_D = 10% of the terms, r = 4 steps)."""
+    import paper_2504_17881_gb300 as ps
+    from paper_2504_17881_gb300 import inputs
+    rng = np.random.default_rng(seed)
+    runs = []
+    for i in range(nruns):
+        n = int(rng.integers(14, 23))
+        L = int(rng.integers(200, 2001))
+        cnt = int(rng.integers(2000, 20001))
+        x, z, h = inputs.jw_hamiltonian(n, L, seed=seed * 100000 + i)
+        H = ps.Hamiltonian(n, x, z, h)
+        if i % 2 == 0:
+            xs, zs, ph = H.qdrift_stream(T_TOTAL, cnt, seed * 100000 + i)
+            kind = "qdrift"
+        else:
+            LD = max(1, L // 10)
+            xs, zs, ph = H.partial_stream(LD, T_TOTAL, 4, max(1, cnt // 4 - LD), seed * 100000 + i)
+            kind = "partial"
+        H.close()
+        runs.append(dict(n=n, x=xs, z=zs, phi=ph, kind=kind, det_seed=seed * 100000 + i))
+    return runs
+
+
+def run_batched(args):
+    import torch
+    import paper_2504_17881_gb300 as ps
+    from paper_2504_17881_gb300 import autotune, inputs
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    t_host = time.perf_counter()
+    runs = batched_workload(args.batch_runs, BATCH_SEED + 1000 * rank)
+    host_gen_s = time.perf_counter() - t_host
+
+    def psi0_for(r, dtype):
+        idx, amp = inputs.determinant_state(r["n"], seed=r["det_seed"])
+        t = torch.zeros(1 << r["n"], dtype=dtype, device=dev)
+        t[torch.as_tensor(idx.astype(np.int64), device=dev)] = torch.as_tensor(amp, device=dev).to(dtype)
+        return t
+
+    for r in runs:
+        r["psi0"] = psi0_for(r, torch.complex64)
+    tune = None
+    cfg = None
+    if not args.no_autotune:
+        tune = autotune.tune_batch(runs, torch.complex64)
+        cfg = {"lane_size": tune["lane_size"], "tile_bits": tune["tile_bits"]}
+    t_host = time.perf_counter()
+    b = ps.Batch(runs, cfg=cfg)
+    create_s = time.perf_counter() - t_host
+    info = b.info
+    for _ in range(args.warmup):
+        b.launch()
+    b.wait()
+
+    clocks = ClockSampler(local)
+    torch.cuda.synchronize(dev)
+    if dist is not None:
+        dist.barrier()
+    clocks.start()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        b.launch()
+    ev1.record(stream)
+    g64 = b.wait()
+    clock_info = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    t_max = ms
+    if dist is not None:
+        tt = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max = float(tt.item())
+    rot_per_launch = info["rotations"]
+    value = world * args.steps * rot_per_launch / (t_max / 1e3)
+    amp_updates = world * args.steps * info["amplitude_rotations"] / (t_max / 1e3)
+    pass_bytes = 2.0 * 8.0 * info["amplitude_passes"]
+    achieved = pass_bytes / (ms / args.steps / 1e3) / 1e9
+    peak, peak_kind = hbm_peak()
+
+    # one run at a time through the public single-run API (plans prebuilt,
+    # like the batch's windows): copy psi0, apply, overlap
+    seq = None
+    if not args.no_sequential:
+        plans = [ps.Plan(r["n"], ps.PS_C64, r["x"], r["z"], r["phi"]) for r in runs]
+        svs = {}
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        for rep in range(2):  # the first pass warms up
+            torch.cuda.synchronize(dev)
+            e0.record(stream)
+            for r, pl in zip(runs, plans):
+                n = r["n"]
+                if n not in svs:
+                    svs[n] = (ps.StateVector(n, tensor=torch.empty(1 << n, dtype=torch.complex64, device=dev)),
+                              ps.StateVector(n, tensor=torch.empty(1 << n, dtype=torch.complex64, device=dev)))
+                st, p0 = svs[n]
+                p0.tensor.copy_(r["psi0"])  # p0 never evolves: its stored scale stays 1
+                st.copy_from(p0)
+                st.apply_plan(pl)
+                st.overlap(p0)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+        seq_ms = e0.elapsed_time(e1)
+        seq = {"ms": seq_ms, "value": rot_per_launch / (seq_ms / 1e3), "unit": UNIT,
+               "how": "512 x (copy psi0, ps_plan_apply of the run's prebuilt plan, ps_overlap), default tuning",
+               "speedup_batch_vs_sequential": seq_ms / (ms / args.steps)}
+        del plans, svs
+
+    # complex64 vs complex128 (the batch engine in FP64 on the same runs)
+    c128 = None
+    if world == 1:
+        runs128 = [dict(r, psi0=psi0_for(r, torch.complex128), state=None) for r in runs]
+        for r in runs:
+            r.pop("psi0", None)
+        b.close()
+        torch.cuda.empty_cache()
+        cfg128 = dict(cfg, tile_bits=min(cfg["tile_bits"], 12)) if cfg else None
+        b128 = ps.Batch(runs128, dtype=torch.complex128, cfg=cfg128)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        b128.launch()
+        b128.wait()
+        e0.record(stream)
+        b128.launch()
+        e1.record(stream)
+        g128 = b128.wait()
+        ms128 = e0.elapsed_time(e1)
+        d = np.abs(g64 - g128)
+        c128 = {"value": rot_per_launch / (ms128 / 1e3), "unit": UNIT, "ms": ms128,
+                "overlap_max_abs_diff_c64_vs_c128": float(d.max()), "overlap_median_abs_diff": float(np.median(d))}
+        b128.close()
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+    ns = [r["n"] for r in runs]
+    line = {
+        "metric": "batched independent runs: rotations/s (qDRIFT and partially randomised, n 14..22, "
+                  "one persistent launch per step)",
+        "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": t_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"{len(runs)} runs, n uniform 14..22 (mean state {np.mean([8 << n for n in ns]) / 2**20:.1f} MiB), "
+                               "200-2000 JW-like terms, 2000-20000 rotations, half qDRIFT half partial (L_D 10%, r 4), "
+                               "8-determinant psi0 per run",
+                   "runs": len(runs), "rotations_per_step": rot_per_launch,
+                   "l2": f"{sum(8 << n for n in ns) / 2**30:.2f} GiB of states per step (> 129 MB L2), no flush",
+                   "batch": {k: info[k] for k in ("grid", "ctas_per_sm", "lanes", "lane_size", "tile_bits",
+                                                    "lane_runs", "single_runs", "resident_runs", "windows", "graph",
+                                                    "smem_bytes", "body_bytes")},
+                   "parallelism": f"replicas x{world}"},
+        "amplitude_updates_per_s": amp_updates,
+        "roofline": {"bound": "hbm", "kernel": "k_batch<float,3,2>", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "note": "algorithmic bytes = one read + one write of every run's state per window "
+                             "(resident runs stay on chip, lane runs partly in L2)",
+                     "peak_source": peak_kind},
+        "sequential": seq, "c128": c128, "autotune": tune,
+        "host": {"workload_generation_s": host_gen_s, "batch_create_s": create_s},
+        "gpu_launches": args.steps, "clocks": clock_info,
+    }
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
 # -------------------------------------------------------------- reference
 
 def run_reference(args):
@@ -443,6 +631,8 @@ def main():
     N_QUBITS = args.qubits
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batched":
+        run_batched(args)
     else:
         run_ours(args)
 

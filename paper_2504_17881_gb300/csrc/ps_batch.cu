@@ -37,48 +37,41 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
 
 __device__ __forceinline__ int ld_status(const int *p) { return *reinterpret_cast<const volatile int *>(p); }
 
-// Barrier of one lane.  Returns false when this CTA must stop: its wait ran
-// out (the status becomes PS_ERR_TIMEOUT), another CTA reported a failure,
-// or the test hook withholds this CTA's arrival.
-__device__ bool lane_barrier(const BatchArgs &A, int lane, bool withhold) {
-    __shared__ int s_ok;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int ok = 1;
-        if (withhold) {
-            ok = 0;
-        } else {
-            unsigned *ctr = A.lane_ctr + (size_t)lane * kLaneStrideWords;
-            unsigned *gen = A.lane_gen + (size_t)lane * kLaneStrideWords;
-            // the generation cannot move before this CTA arrives
-            const unsigned g = ld_acquire(gen);
-            __threadfence();
-            const unsigned arrived = atomicAdd(ctr, 1u) + 1u;
-            if (arrived == (unsigned)A.lane_size) {
-                atomicExch(ctr, 0u);
-                __threadfence();
-                atomicAdd(gen, 1u);
-            } else {
-                const unsigned long long t0 = global_ns();
-                while (ld_acquire(gen) == g) {
-                    if (ld_status(A.status) != PS_OK) {
-                        ok = 0;
-                        break;
-                    }
-                    if (global_ns() - t0 > (unsigned long long)A.budget_ns) {
-                        atomicCAS(A.status, PS_OK, PS_ERR_TIMEOUT);
-                        ok = 0;
-                        break;
-                    }
-                    __nanosleep(100);
-                }
+// Barrier of one lane, called by thread 0 of each member after a
+// __syncthreads (so the stores of all the CTA's threads precede its fence).
+// Returns false when this CTA must stop: its wait ran out (the status
+// becomes PS_ERR_TIMEOUT), another CTA reported a failure, or the test hook
+// withholds this CTA's arrival.
+__device__ bool lane_barrier0(const BatchArgs &A, int lane, bool withhold) {
+    if (withhold) return false;
+    unsigned *ctr = A.lane_ctr + (size_t)lane * kLaneStrideWords;
+    unsigned *gen = A.lane_gen + (size_t)lane * kLaneStrideWords;
+    bool ok = true;
+    // the generation cannot move before this CTA arrives
+    const unsigned g = ld_acquire(gen);
+    __threadfence();
+    const unsigned arrived = atomicAdd(ctr, 1u) + 1u;
+    if (arrived == (unsigned)A.lane_size) {
+        atomicExch(ctr, 0u);
+        __threadfence();
+        atomicAdd(gen, 1u);
+    } else {
+        const unsigned long long t0 = global_ns();
+        while (ld_acquire(gen) == g) {
+            if (ld_status(A.status) != PS_OK) {
+                ok = false;
+                break;
             }
-            __threadfence();
+            if (global_ns() - t0 > (unsigned long long)A.budget_ns) {
+                atomicCAS(A.status, PS_OK, PS_ERR_TIMEOUT);
+                ok = false;
+                break;
+            }
+            __nanosleep(100);
         }
-        s_ok = ok;
     }
-    __syncthreads();
-    return s_ok != 0;
+    __threadfence();
+    return ok;
 }
 
 // Copy a packed window (head, rounds, rotations) into the CTA's TileParams.
@@ -162,102 +155,251 @@ __device__ void cta_store(const C *tile, C *out, size_t count) {
 // The CTA's copy of the current window.
 __shared__ TileParams g_window;
 
-// All windows of run r on this CTA: tiles member, member + S, ... of every
-// window, then the lane barrier (lane >= 0).  A resident run (lane -2) has
-// one tile per window, the whole state, which stays in shared memory: only
-// the first window loads it, no window stores it.  One call site of the tile
-// pass for every kind of run keeps the kernel's code (and its registers) to
-// one copy of the pass.  Returns false when the CTA must stop.
-template <typename R, int G, int NG>
-__device__ __noinline__ bool run_windows(const BatchArgs &A, int r, int lane, int member, int S, bool withhold) {
-    using C = typename CT<R>::T;
-    const BatchRun run = A.runs[r];
-    C *state = reinterpret_cast<C *>(A.states[r]);
-    const C *psi0 = reinterpret_cast<const C *>(A.psi0[r]);
-    const bool resident = run.lane == -2;
-    for (uint32_t w = 0; w < run.nwin; ++w) {
-        const BatchWin bw = A.wins[run.win_off + w];
-        load_window(g_window, A.bodies + bw.body, bw.nsub, bw.nrot);
-        const C *src = (w == 0 && psi0) ? psi0 : state;
-        const uint32_t ntile = 1u << (run.n - bw.B);
-        for (uint32_t h = (uint32_t)member; h < ntile; h += (uint32_t)S)
-            tile_pass<R, G, NG, true>(src, state, g_window, h, run.n, (R)bw.kdelta, !resident || w == 0, !resident);
-        if (lane >= 0 && !lane_barrier(A, lane, withhold)) return false;
+// What the whole CTA does next, decided by thread 0.
+enum : int { kOpDone = 0, kOpWindow, kOpTile, kOpTileGen, kOpLanePartial, kOpSingleEnd };
+
+struct Item {
+    int op;
+    int r;          // run
+    uint32_t h;     // kOpTile*: first tile, step and end of this CTA's tiles
+    uint32_t hstep, ntile;
+    int n;
+    int flags;      // kOpTileGen: bit 0 load, bit 1 store to global; kOpSingleEnd: bit 0 resident
+    int nwin;
+    int nsub, nrot; // kOpWindow
+    const void *src;
+    void *dst;
+    const unsigned char *body;
+    double kdelta;
+    uint64_t b0, b1;  // kOpLanePartial: slice of the state
+    double *partial;  // kOpLanePartial: where thread 0 writes (re, im)
+};
+
+// Thread 0's position in its work: lane runs first, then single runs from
+// the queue.
+struct Cursor {
+    int phase;  // 0 lane runs, 1 queue, 2 done
+    int stage;  // 0 next run, 1 next window, 2 tiles of the window, 3 overlap partial, 4 overlap sum,
+                // 5 end of window
+    int lane, member, S, withhold;
+    int q, q_end, r;
+    int n, kind, nwin;
+    uint32_t w, win_off, h, ntile;
+    int B;
+    double kdelta;
+    const void *psi0;
+    void *state;
+};
+
+// Advance the cursor to the next item of the CTA (thread 0 only; lane
+// barriers wait here while the other threads wait at the CTA barrier).
+template <int G, int NG>
+__device__ void next_item(const BatchArgs &A, Cursor &cu, Item &it) {
+    for (;;) {
+        if (cu.phase == 2) {
+            it.op = kOpDone;
+            return;
+        }
+        switch (cu.stage) {
+        case 0: {  // next run
+            if (cu.phase == 0) {
+                if (cu.q >= cu.q_end) {
+                    cu.phase = 1;
+                    continue;
+                }
+                cu.r = A.lane_runs[cu.q];
+            } else {
+                if (ld_status(A.status) != PS_OK) {
+                    cu.phase = 2;
+                    continue;
+                }
+                const unsigned slot = atomicAdd(A.queue, 1u);
+                if (slot >= (unsigned)A.nsingle) {
+                    cu.phase = 2;
+                    continue;
+                }
+                cu.r = A.single_order[slot];
+            }
+            const BatchRun run = A.runs[cu.r];
+            cu.n = run.n;
+            cu.kind = run.lane;
+            cu.nwin = (int)run.nwin;
+            cu.win_off = run.win_off;
+            cu.state = A.states[cu.r];
+            cu.psi0 = A.psi0[cu.r];
+            cu.w = 0;
+            cu.stage = 1;
+            continue;
+        }
+        case 1: {  // next window
+            if (cu.w >= (uint32_t)cu.nwin) {
+                if (cu.phase == 0) {
+                    cu.stage = 3;
+                    continue;
+                }
+                it.op = kOpSingleEnd;
+                it.r = cu.r;
+                it.n = cu.n;
+                it.nwin = cu.nwin;
+                it.flags = cu.kind == -2 ? 1 : 0;
+                it.src = cu.psi0;
+                it.dst = cu.state;
+                cu.stage = 0;
+                return;
+            }
+            const BatchWin bw = A.wins[cu.win_off + cu.w];
+            cu.kdelta = bw.kdelta;
+            cu.B = bw.B;
+            cu.ntile = 1u << (cu.n - bw.B);
+            cu.h = cu.phase == 0 ? (uint32_t)cu.member : 0u;
+            cu.stage = 2;
+            it.op = kOpWindow;
+            it.body = A.bodies + bw.body;
+            it.nsub = bw.nsub;
+            it.nrot = bw.nrot;
+            return;
+        }
+        case 2: {  // this CTA's tiles of the window, all in one item
+            const bool resident = cu.kind == -2;
+            // a full block of register groups: 2^(B - G) / NG >= kBatchThreads
+            const bool full = !resident && cu.B - G - (NG == 4 ? 2 : NG == 2 ? 1 : 0) >= 8;
+            it.op = full ? kOpTile : kOpTileGen;
+            it.h = cu.h;
+            it.hstep = cu.phase == 0 ? (uint32_t)cu.S : 1u;
+            it.ntile = cu.ntile;
+            it.n = cu.n;
+            it.kdelta = cu.kdelta;
+            it.src = (cu.w == 0 && cu.psi0) ? cu.psi0 : cu.state;
+            it.dst = cu.state;
+            it.flags = ((!resident || cu.w == 0) ? 1 : 0) | (resident ? 0 : 2);
+            cu.stage = 5;
+            return;
+        }
+        case 5: {  // end of window: lane barrier before the next window reads
+            if (cu.phase == 0 && !lane_barrier0(A, cu.lane, cu.withhold != 0)) {
+                cu.phase = 2;
+                continue;
+            }
+            cu.w++;
+            cu.stage = 1;
+            continue;
+        }
+        case 3: {  // overlap: this member's slice
+            if (!cu.psi0) {
+                cu.q++;
+                cu.stage = 0;
+                continue;
+            }
+            const uint64_t N = 1ull << cu.n;
+            const uint64_t per = (N + cu.S - 1) / cu.S;
+            it.op = kOpLanePartial;
+            it.r = cu.r;
+            it.nwin = cu.nwin;
+            it.src = cu.psi0;
+            it.dst = cu.state;
+            it.b0 = min(N, per * (uint64_t)cu.member);
+            it.b1 = min(N, it.b0 + per);
+            // two buffers: a member may start the next run's partial while
+            // member 0 still sums this one's
+            it.partial = A.partials + 2 * ((size_t)(cu.q & 1) * A.nlanes * cu.S + (size_t)cu.lane * cu.S + cu.member);
+            cu.stage = 4;
+            return;
+        }
+        case 4: {  // overlap: member 0 sums the partials in member order
+            if (!lane_barrier0(A, cu.lane, cu.withhold != 0)) {
+                cu.phase = 2;
+                continue;
+            }
+            if (cu.member == 0) {
+                const double *pp = A.partials + 2 * ((size_t)(cu.q & 1) * A.nlanes * cu.S + (size_t)cu.lane * cu.S);
+                double re = 0.0, im = 0.0;
+                for (int m = 0; m < cu.S; ++m) {
+                    re += __ldcg(pp + 2 * m);
+                    im += __ldcg(pp + 2 * m + 1);
+                }
+                A.overlaps[2 * cu.r] = re;
+                A.overlaps[2 * cu.r + 1] = im;
+            }
+            cu.q++;
+            cu.stage = 0;
+            continue;
+        }
+        default:
+            cu.phase = 2;
+            continue;
+        }
     }
-    return true;
 }
 
+// Persistent CTA: thread 0 picks the next item, the whole CTA executes it.
+// No loop state lives in registers across a tile pass (it is all in the
+// shared cursor), so each pass has the single-window kernel's register
+// budget to itself.
 template <typename R, int G, int NG>
 __global__ void __launch_bounds__(kBatchThreads, tile_min_blocks<R, G, NG>()) k_batch(const __grid_constant__ BatchArgs A) {
     using C = typename CT<R>::T;
     extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ unsigned s_slot;
-    const int S = A.lane_size;
-    const int lane = (int)blockIdx.x / S, member = (int)blockIdx.x % S;
-
-    // ---------------------------------------------------------- lane runs
-    if (lane < A.nlanes) {
-        const bool withhold = A.withhold && lane == 0 && member == S - 1 && S > 1;
-        for (int q = A.lane_off[lane]; q < A.lane_off[lane + 1]; ++q) {
-            const int r = A.lane_runs[q];
-            if (!run_windows<R, G, NG>(A, r, lane, member, S, withhold)) return;
-            const C *psi0 = reinterpret_cast<const C *>(A.psi0[r]);
-            if (!psi0) continue;
-            C *state = reinterpret_cast<C *>(A.states[r]);
-            const BatchRun run = A.runs[r];
-            // member m sums its slice; partials alternate between two buffers
-            // so a member may start the next run's epilogue while member 0
-            // still reads this one's
-            const size_t N = (size_t)1 << run.n;
-            const size_t per = (N + S - 1) / S;
-            const size_t b0 = min(N, per * member), b1 = min(N, b0 + per);
-            const double2 p = cta_overlap<C>(psi0, state, run.nwin == 0 ? state : nullptr, b0, b1, run.nwin == 0);
-            double *part = A.partials + 2 * ((size_t)(q & 1) * A.nlanes * S + (size_t)lane * S + member);
-            if (threadIdx.x == 0) {
-                part[0] = p.x;
-                part[1] = p.y;
-            }
-            if (!lane_barrier(A, lane, withhold)) return;
-            if (member == 0 && threadIdx.x == 0) {
-                const double *pp = A.partials + 2 * ((size_t)(q & 1) * A.nlanes * S + (size_t)lane * S);
-                double re = 0.0, im = 0.0;
-                for (int m = 0; m < S; ++m) {
-                    re += __ldcg(pp + 2 * m);
-                    im += __ldcg(pp + 2 * m + 1);
-                }
-                A.overlaps[2 * r] = re;
-                A.overlaps[2 * r + 1] = im;
-            }
+    __shared__ Cursor cu;
+    __shared__ Item it;
+    if (threadIdx.x == 0) {
+        const int S = A.lane_size;
+        cu.S = S;
+        cu.lane = (int)blockIdx.x / S;
+        cu.member = (int)blockIdx.x % S;
+        cu.withhold = (A.withhold && cu.lane == 0 && cu.member == S - 1 && S > 1) ? 1 : 0;
+        cu.stage = 0;
+        if (cu.lane < A.nlanes) {
+            cu.phase = 0;
+            cu.q = A.lane_off[cu.lane];
+            cu.q_end = A.lane_off[cu.lane + 1];
+        } else {
+            cu.phase = 1;
         }
     }
-
-    // --------------------------------------------------------- single runs
     for (;;) {
         __syncthreads();
-        if (threadIdx.x == 0) s_slot = atomicAdd(A.queue, 1u);
+        if (threadIdx.x == 0) next_item<G, NG>(A, cu, it);
         __syncthreads();
-        const unsigned slot = s_slot;
-        if (slot >= (unsigned)A.nsingle) break;
-        if (ld_status(A.status) != PS_OK) break;
-        const int r = A.single_order[slot];
-        run_windows<R, G, NG>(A, r, -1, 0, 1, false);
-        __syncthreads();
-        const BatchRun run = A.runs[r];
-        C *state = reinterpret_cast<C *>(A.states[r]);
-        const C *psi0 = reinterpret_cast<const C *>(A.psi0[r]);
-        const size_t N = (size_t)1 << run.n;
-        const C *tile = reinterpret_cast<const C *>(smem);
-        const bool resident = run.lane == -2 && run.nwin > 0;
-        if (psi0) {
-            // a resident run leaves shared memory on the way
-            const double2 p = cta_overlap<C>(psi0, resident ? tile : state,
-                                             (resident || run.nwin == 0) ? state : nullptr, 0, N, run.nwin == 0);
+        const int op = it.op;
+        if (op == kOpDone) break;
+        if (op == kOpTile) {
+            // only h stays in a register across a pass; the rest is re-read
+            // from shared memory after the pass's barriers
+            for (uint32_t h = it.h; h < it.ntile; h += it.hstep)
+                tile_pass<R, G, NG, false>(reinterpret_cast<const C *>(it.src), reinterpret_cast<C *>(it.dst),
+                                           g_window, h, it.n, (R)it.kdelta, true, true);
+        } else if (op == kOpTileGen) {
+            for (uint32_t h = it.h; h < it.ntile; h += it.hstep)
+                tile_pass<R, G, NG, true>(reinterpret_cast<const C *>(it.src), reinterpret_cast<C *>(it.dst),
+                                          g_window, h, it.n, (R)it.kdelta, (it.flags & 1) != 0, (it.flags & 2) != 0);
+        } else if (op == kOpWindow) {
+            load_window(g_window, it.body, it.nsub, it.nrot);
+        } else if (op == kOpLanePartial) {
+            const bool copy = it.nwin == 0;
+            C *state = reinterpret_cast<C *>(it.dst);
+            const double2 p = cta_overlap<C>(reinterpret_cast<const C *>(it.src), state, copy ? state : nullptr,
+                                             it.b0, it.b1, copy);
             if (threadIdx.x == 0) {
-                A.overlaps[2 * r] = p.x;
-                A.overlaps[2 * r + 1] = p.y;
+                it.partial[0] = p.x;
+                it.partial[1] = p.y;
             }
-        } else if (resident) {
-            cta_store<C>(tile, state, N);
+        } else if (op == kOpSingleEnd) {
+            const C *psi0 = reinterpret_cast<const C *>(it.src);
+            C *state = reinterpret_cast<C *>(it.dst);
+            const size_t N = (size_t)1 << it.n;
+            const C *tile = reinterpret_cast<const C *>(smem);
+            const bool resident = (it.flags & 1) && it.nwin > 0;
+            if (psi0) {
+                // a resident run leaves shared memory on the way
+                const double2 p = cta_overlap<C>(psi0, resident ? tile : state,
+                                                 (resident || it.nwin == 0) ? state : nullptr, 0, N, it.nwin == 0);
+                if (threadIdx.x == 0) {
+                    A.overlaps[2 * it.r] = p.x;
+                    A.overlaps[2 * it.r + 1] = p.y;
+                }
+            } else if (resident) {
+                cta_store<C>(tile, state, N);
+            }
         }
     }
 }

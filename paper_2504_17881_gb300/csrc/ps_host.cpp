@@ -56,6 +56,7 @@ void fill_tile_params(const Plan &p, const WinDesc &w, TileParams &tp) {
         tp.sub[s].r0 = (uint8_t)(sd.rot_off - w.rot_off);
         tp.sub[s].r1 = (uint8_t)(sd.rot_off - w.rot_off + sd.nrot);
         tp.sub[s].fast = sd.fast;
+        tp.sub[s].pad = 0;
     }
     for (int r = 0; r < w.nrot; ++r) {
         const RotDesc &rd = p.rot[w.rot_off + r];

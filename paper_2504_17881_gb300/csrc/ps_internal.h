@@ -114,13 +114,17 @@ struct TileRotP {
     uint32_t pad;
 };
 
-struct TileSubP {
+// 32 bytes, 16-byte aligned: a pass reads a round's descriptor as two
+// 16-byte vectors.
+struct alignas(16) TileSubP {
     uint32_t u[kMaxG];  // group basis in tile coordinates
     int8_t piv[kMaxG];  // echelon pivots of span(u), ascending
     uint8_t r0, r1;     // rotations [r0, r1) of the window
     uint8_t fast;       // k > 0: the round is k tangent-form rotations with an even number
                         // of Y factors whose group X masks are 1, 2, 4, ..., 2^(k-1) in order
+    uint32_t pad;
 };
+static_assert(sizeof(TileSubP) == 32 && kMaxG == 5, "round descriptor layout read as two 16-byte vectors");
 
 struct TileParams {
     uint64_t v[kMaxD];  // window basis, v[i] <-> tile bit c + i

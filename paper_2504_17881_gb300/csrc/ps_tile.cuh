@@ -196,6 +196,12 @@ constexpr int tile_min_blocks() {
     return (NG << G) * (int)sizeof(R) <= 64 ? 3 : 2;
 }
 
+// Per-pass tables of a CTA, one copy for every instance of the pass:
+// V over each 4-bit nibble of a segment index, and the global offsets W_i of
+// the current round's group basis.
+static __shared__ uint64_t g_pass_nib[4][16];
+static __shared__ uint64_t g_pass_sub_w[kParamSub][kMaxG];
+
 // One tile pass: coset H of the window P (n-qubit state), read from src and
 // written to dst (the same buffer for an in-place pass).  Used by k_tile (one
 // tile per CTA) and by the batched kernel (many tiles per CTA); the leading
@@ -217,8 +223,8 @@ __device__ __forceinline__ void tile_pass(const typename CT<R>::T *src, typename
     using C = typename CT<R>::T;
     constexpr int LS = sizeof(C) == 8 ? 3 : 4;  // log2 bytes per amplitude
     extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ uint64_t nib[4][16];            // V over each 4-bit nibble of a segment index
-    __shared__ uint64_t sub_w[kParamSub][kMaxG];
+    uint64_t (&nib)[4][16] = g_pass_nib;
+    uint64_t (&sub_w)[kParamSub][kMaxG] = g_pass_sub_w;
     __syncthreads();
     const int c = P.c, d = P.d;
     const int B = c + d;
@@ -251,9 +257,17 @@ __device__ __forceinline__ void tile_pass(const typename CT<R>::T *src, typename
         const int it_shift = lgB - seg_log;
         const uint64_t base = k0 ^ v_of(P, (uint32_t)tid >> seg_log);
         const uint64_t off = (uint64_t)((uint32_t)tid & ((1u << seg_log) - 1)) << 4;
+        // Gray steps 1, 2, 1 of every group of four iterations use v[it_shift]
+        // and v[it_shift + 1] from registers; only the fourth reads the window
+        const uint64_t va = niter > 1 ? P.v[it_shift] : 0, vb = niter > 2 ? P.v[it_shift + 1] : 0;
         uint64_t vi = 0;
         for (int i = 0; i < niter; ++i) {
-            if (i) vi ^= P.v[it_shift + (__ffs(i) - 1)];
+            if (i & 1)
+                vi ^= va;
+            else if (i & 2)
+                vi ^= vb;
+            else if (i)
+                vi ^= P.v[it_shift + (__ffs(i) - 1)];
             const int gi = i ^ (i >> 1);
             cp_async16(smem + (size_t)(tid + (gi << lgB)) * 16, gbase + ((base ^ vi) << LS) + off);
         }
@@ -307,15 +321,19 @@ __device__ __forceinline__ void tile_pass(const typename CT<R>::T *src, typename
     const bool idx32 = n <= 32;
     for (int si = 0; si < nsub; ++si) {
         const bool last = si == nsub - 1;
-        const TileSubP &sp = P.sub[si];
+        // the round's descriptor as two 16-byte vectors: u[0..3] | u[4], piv[0..3], piv[4] r0 r1 fast, pad
+        const uint4 d0 = reinterpret_cast<const uint4 *>(&P.sub[si])[0];
+        const uint4 d1 = reinterpret_cast<const uint4 *>(&P.sub[si])[1];
+        const uint32_t uw[5] = {d0.x, d0.y, d0.z, d0.w, d1.x};
         uint32_t ub[G];
         int piv[G];
 #pragma unroll
         for (int i = 0; i < G; ++i) {
-            ub[i] = sp.u[i];
-            piv[i] = sp.piv[i];
+            ub[i] = uw[i];
+            piv[i] = (int)(int8_t)((i < 4 ? d1.y >> (8 * i) : d1.z) & 0xffu);
         }
-        const int r0 = sp.r0, r1 = sp.r1;
+        const int r0 = (int)((d1.z >> 8) & 0xffu), r1 = (int)((d1.z >> 16) & 0xffu);
+        const int fast_k = (int)(d1.z >> 24);
         // One batch of NG register groups: load from the tile, rotate, store.
         // A full standard round (K = G rotations, the common case) gets its
         // own copy of the whole body so its registers never meet the general
@@ -418,7 +436,7 @@ __device__ __forceinline__ void tile_pass(const typename CT<R>::T *src, typename
                 }
             }
         };
-        const bool full = sp.fast == G;
+        const bool full = fast_k == G;
         if (!GEN || tid < T) {
             for (int bt = 0; bt < nbatch; ++bt) {
                 if (full)
