@@ -1,0 +1,135 @@
+"""Pins of the learned-step-choice oracle (oracle/learned.py), CPU only.
+
+Each check ties the oracle to something other than itself: dense Pauli
+matrices, closed forms of the bound on small Hamiltonians, a hand-computed
+feature vector, central finite differences of the loss, and the closed form of
+Adam's first step.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import learned as L
+
+I2 = np.eye(2, dtype=complex)
+PX = np.array([[0, 1], [1, 0]], dtype=complex)
+PY = np.array([[0, -1j], [1j, 0]], dtype=complex)
+PZ = np.array([[1, 0], [0, -1]], dtype=complex)
+
+
+def dense(n, x, z):
+    """Dense matrix of the string: qubit q (bit q) is the q-th factor from the right."""
+    m = np.ones((1, 1), dtype=complex)
+    for q in reversed(range(n)):
+        f = {(0, 0): I2, (1, 0): PX, (0, 1): PZ, (1, 1): PY}[((x >> q) & 1, (z >> q) & 1)]
+        m = np.kron(m, f)
+    return m
+
+
+def test_anticommutation_matches_dense_matrices():
+    n = 2
+    for x1 in range(4):
+        for z1 in range(4):
+            for x2 in range(4):
+                for z2 in range(4):
+                    A, B = dense(n, x1, z1), dense(n, x2, z2)
+                    anti = np.allclose(A @ B, -(B @ A))
+                    comm = np.allclose(A @ B, B @ A)
+                    assert anti != comm
+                    assert L.anticommute(n, x1, z1, x2, z2) == anti
+    rng = np.random.default_rng(0)
+    for _ in range(60):
+        x1, z1, x2, z2 = (int(v) for v in rng.integers(0, 16, size=4))
+        A, B = dense(4, x1, z1), dense(4, x2, z2)
+        assert L.anticommute(4, x1, z1, x2, z2) == np.allclose(A @ B, -(B @ A))
+
+
+def test_bound_closed_forms():
+    a, b = 0.7, -0.3
+    # H = a X + b Z on one qubit: the two terms anticommute
+    x, z, h = [1, 0], [0, 1], [a, b]
+    assert L.trotter_bound(1, x, z, h) == pytest.approx(8 * abs(a) * abs(b), rel=1e-15)
+    # only the larger term deterministic: the randomised-part terms of the bound
+    big, small = abs(a), abs(b)
+    assert L.trotter_bound(1, x, z, h, L_D=1) == pytest.approx(small * big ** 2 + big * small ** 2, rel=1e-15)
+    # everything randomised: lambda_R = lambda and both randomised-part terms vanish
+    assert L.trotter_bound(1, x, z, h, L_D=0) == 0.0
+    # mutually commuting terms: no deterministic contribution
+    assert L.trotter_bound(2, [0, 0, 0], [1, 2, 3], [0.5, -0.2, 0.1]) == 0.0
+    # {X1X2, Z1Z2, Y1Y2} commute pairwise
+    assert L.trotter_bound(2, [3, 0, 3], [0, 3, 3], [0.4, 0.3, -0.2]) == 0.0
+
+
+def test_features_hand_example():
+    # n = 2: 0.5 X1, -0.25 Z1 Z2, 0.25 Y2
+    n, x, z, h = 2, [1, 0, 2], [0, 3, 2], [0.5, -0.25, 0.25]
+    t, r = 0.8, 4
+    f = L.features(n, x, z, h, t, r)
+    lam = 1.0
+    # anticommuting pairs: X1 with Z1Z2 (qubit 1: X vs Z), Z1Z2 with Y2 (qubit 2: Z vs Y); X1 and Y2 commute
+    C = 4 * (0.5 * 0.25 + 0.25 * (0.5 + 0.25) + 0.25 * 0.25)
+    expect = [2 / 32, math.log(3), math.log(lam), math.log(0.5), math.log(t), math.log(r), math.log(C),
+              math.log(C * t * t / r), 0.25, (0.5 * 1 + 0.25 * 2 + 0.25 * 1) / (lam * 2)]
+    assert np.allclose(f, expect, rtol=1e-14, atol=1e-15)
+
+
+def rand_params(n_in, width, seed, scale=0.6):
+    rng = np.random.default_rng(seed)
+    size = sum(int(np.prod(s)) for _, s in L.param_shapes(n_in, width))
+    return rng.normal(0, scale, size=size)
+
+
+def test_backprop_matches_central_differences():
+    n_in, width = 3, 6
+    p = rand_params(n_in, width, 1)
+    rng = np.random.default_rng(2)
+    X = rng.normal(size=(7, n_in))
+    T = rng.normal(size=7)
+    loss, g = L.loss_and_grad(p, X, T, n_in, width)
+    eps = 1e-6
+    fd = np.zeros_like(p)
+    for j in range(len(p)):
+        q = p.copy()
+        q[j] += eps
+        lp, _ = L.loss_and_grad(q, X, T, n_in, width)
+        q[j] -= 2 * eps
+        lm, _ = L.loss_and_grad(q, X, T, n_in, width)
+        fd[j] = (lp - lm) / (2 * eps)
+    assert np.max(np.abs(fd - g)) < 1e-7 * max(1.0, np.max(np.abs(g)))
+
+
+def test_forward_closed_forms():
+    n_in, width = 2, 4
+    size = sum(int(np.prod(s)) for _, s in L.param_shapes(n_in, width))
+    p = L.unpack(np.zeros(size), n_in, width)
+    p["b_out"][0] = 0.37
+    X = np.array([[1.0, -2.0], [0.5, 3.0]])
+    out, _ = L.forward(L.pack(p, n_in, width), X, n_in, width)
+    assert np.allclose(out, 0.37)
+    # one path through the first unit of every layer
+    p = L.unpack(np.zeros(size), n_in, width)
+    p["W1"][0, 0] = 1.0
+    p["W2"][0, 0] = 1.0
+    p["W3"][0, 0] = 1.0
+    p["w_out"][0] = 1.0
+    out, _ = L.forward(L.pack(p, n_in, width), X, n_in, width)
+    assert np.allclose(out, np.tanh(np.tanh(np.tanh(X[:, 0]))), rtol=1e-15)
+
+
+def test_adam_first_step_closed_form():
+    rng = np.random.default_rng(3)
+    p = rng.normal(size=20)
+    g = rng.normal(size=20)
+    z = np.zeros(20)
+    lr, eps = 0.01, 1e-8
+    p1, m1, v1 = L.adam_step(p, g, z, z, 1, lr, eps=eps)
+    # first step: the bias-corrected moments are g and g^2
+    assert np.allclose(p1, p - lr * g / (np.abs(g) + eps), rtol=1e-14, atol=1e-16)
+    # a constant gradient moves every parameter by about lr per step
+    q, m, v = p, z, z
+    for s in range(1, 200):
+        q_new, m, v = L.adam_step(q, g, m, v, s, lr, eps=eps)
+        step = q - q_new
+        q = q_new
+    assert np.allclose(step, lr * np.sign(g), rtol=1e-6)
