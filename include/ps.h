@@ -361,6 +361,115 @@ void ps_batch_destroy(ps_batch *b);
 int ps_batch_describe(int dtype, const ps_run_desc *runs, size_t nruns, const ps_batch_config *cfg, int num_sms,
                       int ctas_per_sm, ps_batch_info *out, int *lane_of, int *tile_bits_of, uint64_t *windows_of);
 
+/* --------------------------------------------------- learned step choice
+ *
+ * The paper's error target (eps = 0.001, Methods, "Hamiltonian simulation")
+ * fixes the Trotter step count r through the error prefactor, whose analytic
+ * bound (Methods, "Data analysis") it finds one to two orders of magnitude
+ * too large (Results).  Here a small network predicts the natural log of the
+ * empirical first-order Trotter error of the overlap,
+ *     eps(H, t, r) = |<psi|U_r(t)|psi> - <psi|exp(itH)|psi>|,
+ * from ten features of the query, trained on errors the simulator itself
+ * produces; r is then the smallest step count whose prediction is at most
+ * log(eps) - margin.  The plain doubling sweep (ps_trotter_sweep) is the
+ * fallback and the judge.
+ */
+#define PS_MLP_FEATURES 12
+
+/* The bound on the Trotter-error prefactor of the partially randomised
+ * decomposition with deterministic part D = the first L_D terms by
+ * decreasing |h| (ties in input order) and randomised one-norm lambda_R:
+ *   4 sum_{l in D} |h_l| sum_{k in D, P_k anticommutes with P_l} |h_k|
+ *     + lambda_R (lambda - lambda_R)^2 + (lambda - lambda_R) lambda_R^2
+ * (Methods, "Data analysis").  Host only, O(L_D^2). */
+int ps_ham_trotter_bound(const ps_ham *ham, size_t L_D, double *out);
+
+/* The leading coefficient K of the first-order Trotter error of the overlap
+ * for the sparse initial state psi = sum_i amp_i |idx_i> (ndet distinct
+ * basis states; amp holds re, im pairs):
+ *   K = sum_{k < l, P_k P_l = -P_l P_k} h_l h_k <psi|P_l P_k|psi>,
+ * term k applied before term l.  One Trotter step of size delta equals
+ * exp(i delta H - (delta^2 / 2) sum_{l>k} h_l h_k [P_l, P_k] + O(delta^3)),
+ * so g_r(t) - g(t) = -(t^2 / r) K + O(t^3 / r).  out = (re, im).  Cached per
+ * handle for the last state.  Host only, O(L^2) with a cheap rejection of
+ * pairs whose X masks differ by no difference of two basis states of psi. */
+int ps_ham_error_coefficient(ps_ham *ham, const uint64_t *idx, const double *amp, size_t ndet, double *out);
+
+/* PS_MLP_FEATURES floats describing "first-order Trotter with r steps to
+ * time t from psi" (t > 0, r >= 1; psi as for ps_ham_error_coefficient):
+ *   n / 32, log L, log lambda, log(max|h| / lambda), log t, log r, log C,
+ *   log(C t^2 / r), one-norm fraction of diagonal terms (x = 0),
+ *   sum_l |h_l| popc(x_l | z_l) / (lambda n),
+ *   k = log max(|K| / lambda^2, 1e-12),  k + log(lambda^2 t^2 / r),
+ * C = ps_ham_trotter_bound(ham, L) (computed once per handle and cached).
+ * PS_ERR_ARG when every pair of terms commutes (C = 0). Host only. */
+int ps_ham_features(ps_ham *ham, const uint64_t *idx, const double *amp, size_t ndet, double t, uint32_t r,
+                    float *out);
+
+/* The first-order Trotter stream of ps_evolve_trotter: the term list r
+ * times, angle (t / r) h_l; r * L rotations into the caller's arrays. */
+int ps_trotter_stream(const ps_ham *ham, double t, uint32_t r, uint64_t *x_out, uint64_t *z_out, double *phi_out);
+
+/* The plain doubling sweep: g_r = <psi0|U_r(t)|psi0> for r = 1, 2, 4, ...
+ * (each evolved on `work` from a copy of psi0) until 2 |g_r - g_2r| <= eps;
+ * *r_out = that r (0 if 2r would exceed r_max; then PS_ERR_UNSUPPORTED),
+ * *rotations_out = rotations applied in total, g_out = g_r.  Synchronous. */
+int ps_trotter_sweep(ps_state *work, const ps_state *psi0, const ps_ham *ham, double t, double eps, uint32_t r_max,
+                     uint32_t *r_out, uint64_t *rotations_out, double *g_out);
+
+typedef struct ps_mlp ps_mlp; /* opaque: network parameters and Adam state on one device */
+
+/* Training knobs; zero selects the default. */
+typedef struct ps_mlp_train_config {
+    int epochs;      /* default 200 */
+    int batch;       /* rows per Adam step (default 256); an epoch drops its last partial batch */
+    float lr;        /* default 1e-3 */
+    float beta1;     /* default 0.9 */
+    float beta2;     /* default 0.999 */
+    float eps;       /* default 1e-8 */
+    uint64_t seed;   /* shuffling seed (SplitMix64 Fisher-Yates per epoch) */
+} ps_mlp_train_config;
+
+/* A network of n_in (1..16) inputs, three tanh hidden layers of 128 units
+ * and one linear output, FP32, on the current device, ops on `stream`.
+ * Parameters, flat and out-major (W[o][i] at o * fan_in + i):
+ *   W1 (128 x n_in), b1 (128), W2 (128 x 128), b2, W3 (128 x 128), b3,
+ *   w_out (128), b_out (1)   -- ps_mlp_num_params values.
+ * Weights start Glorot-uniform from SplitMix64(seed), biases at zero.
+ * Inputs are standardised per feature, (x - mu) / sigma, and the output is
+ * y_mu + y_sigma * net(x); the loss of training is the mean squared error
+ * of net(x) against (y - y_mu) / y_sigma. */
+int ps_mlp_create(int n_in, uint64_t seed, void *stream, ps_mlp **out);
+void ps_mlp_destroy(ps_mlp *m);
+size_t ps_mlp_num_params(const ps_mlp *m);
+int ps_mlp_get_params(ps_mlp *m, float *host);        /* synchronous */
+int ps_mlp_set_params(ps_mlp *m, const float *host);  /* synchronous */
+int ps_mlp_get_grads(ps_mlp *m, float *host);         /* gradient of the last ps_mlp_loss_grad */
+int ps_mlp_set_normalization(ps_mlp *m, const float *mu, const float *sigma, float y_mu, float y_sigma);
+int ps_mlp_get_normalization(const ps_mlp *m, float *mu, float *sigma, float *y_mu, float *y_sigma);
+/* mu and sigma (population standard deviation; 1 for a constant column) of
+ * the host arrays x (rows x n_in, row-major) and y (rows). */
+int ps_mlp_fit_normalization(ps_mlp *m, const float *x_host, const float *y_host, size_t rows);
+/* Full-batch loss and gradient (kept on the device, read with
+ * ps_mlp_get_grads) for device arrays x (rows x n_in) and y (rows). */
+int ps_mlp_loss_grad(ps_mlp *m, const float *x_dev, const float *y_dev, size_t rows, double *loss_out);
+/* One Adam step (Kingma & Ba, bias-corrected) with the current gradient. */
+int ps_mlp_adam_step(ps_mlp *m, float lr, float beta1, float beta2, float eps);
+/* Mini-batch Adam on device arrays; every epoch is one CUDA graph replay.
+ * loss_per_epoch (epochs floats, may be NULL) receives the mean training
+ * loss of each epoch (synchronising once per epoch). */
+int ps_mlp_train(ps_mlp *m, const float *x_dev, const float *y_dev, size_t rows, const ps_mlp_train_config *cfg,
+                 float *loss_per_epoch);
+/* y_dev[i] = the network's prediction for row i of x_dev (asynchronous). */
+int ps_mlp_predict(ps_mlp *m, const float *x_dev, size_t rows, float *y_dev);
+/* Smallest r in 1..r_max whose predicted log error (a network trained on
+ * log eps with ps_ham_features inputs for the initial state psi) is
+ * <= log(eps) - margin; pred_out (r_max floats, may be NULL) receives every
+ * prediction.  PS_ERR_UNSUPPORTED (r_out = 0) when no r qualifies.
+ * Synchronous. */
+int ps_mlp_pick_r(ps_mlp *m, ps_ham *ham, const uint64_t *idx, const double *amp, size_t ndet, double t, double eps,
+                  double margin, uint32_t r_max, uint32_t *r_out, float *pred_out);
+
 #ifdef __cplusplus
 }
 #endif

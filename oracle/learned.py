@@ -9,7 +9,10 @@ Plain numpy / Python, FP64, written from the definitions:
         C <= 4 sum_{l in D} |h_l| sum_{k in D, [P_l, P_k] != 0} |h_k|
              + lambda_R (lambda - lambda_R)^2 + (lambda - lambda_R) lambda_R^2,
     D = the first L_D terms by decreasing |h| (ties keep input order), R the rest.
-  * The feature vector of a (Hamiltonian, t, r) query (ten numbers).
+  * The leading-order coefficient K of the first-order Trotter error of the
+    overlap (from the second-order term of the product formula's exponent),
+    and the feature vector of a (Hamiltonian, t, r, initial state) query
+    (twelve numbers).
   * A tanh multilayer perceptron with a linear scalar output, its mean-squared
     loss, the gradient by backpropagation, and one Adam step (Kingma & Ba).
 Only ``tests/`` may import this module.  It shares no code with the CUDA
@@ -21,7 +24,8 @@ import math
 
 import numpy as np
 
-N_FEATURES = 10
+N_FEATURES = 12
+K_FLOOR = 1e-12
 
 
 # ------------------------------------------------------------ Pauli algebra
@@ -65,8 +69,35 @@ def trotter_bound(n: int, x, z, h, L_D: int | None = None) -> float:
     return 4.0 * det + lam_R * (lam - lam_R) ** 2 + (lam - lam_R) * lam_R ** 2
 
 
-def features(n: int, x, z, h, t: float, r: int) -> np.ndarray:
-    """Feature vector of the query "first-order Trotter, r steps, time t":
+def pauli_apply(n: int, x: int, z: int, psi: np.ndarray) -> np.ndarray:
+    """P psi from P|k> = i^{popc(x & z)} (-1)^{popc(k & z)} |k ^ x>, basis state by basis state."""
+    out = np.zeros_like(psi)
+    ph = 1j ** (bin(x & z).count("1") % 4)
+    for k in range(1 << n):
+        if psi[k] != 0:
+            out[k ^ x] += ph * (-1) ** (bin(k & z).count("1") % 2) * psi[k]
+    return out
+
+
+def error_coefficient(n: int, x, z, h, psi: np.ndarray) -> complex:
+    """K = sum over pairs k < l (k applied first) of anticommuting terms of
+    h_l h_k <psi|P_l P_k|psi>.  One first-order Trotter step of size delta
+    is exp(i delta H - (delta^2 / 2) sum_{l>k} h_l h_k [P_l, P_k] + ...),
+    and [P_l, P_k] = 2 P_l P_k for anticommuting strings, so for small t
+    g_r - g = -(t^2 / r) K + O(t^3 / r)."""
+    L = len(h)
+    K = 0.0 + 0.0j
+    for k in range(L):
+        pk = pauli_apply(n, int(x[k]), int(z[k]), psi)
+        for l in range(k + 1, L):
+            if anticommute(n, int(x[l]), int(z[l]), int(x[k]), int(z[k])):
+                K += float(h[l]) * float(h[k]) * np.vdot(psi, pauli_apply(n, int(x[l]), int(z[l]), pk))
+    return complex(K)
+
+
+def features(n: int, x, z, h, t: float, r: int, psi: np.ndarray) -> np.ndarray:
+    """Feature vector of the query "first-order Trotter, r steps, time t,
+    initial state psi":
       0  n / 32
       1  log L
       2  log lambda                      (lambda = sum |h|)
@@ -77,6 +108,8 @@ def features(n: int, x, z, h, t: float, r: int) -> np.ndarray:
       7  log(C t^2 / r)                  (the bound's error scale)
       8  sum over diagonal terms (x = 0) of |h| / lambda
       9  sum_l |h_l| |support(P_l)| / (lambda n)
+     10  log(max(|K| / lambda^2, K_FLOOR))     (K = error_coefficient)
+     11  feature 10 + log(lambda^2 t^2 / r)    (the leading-order error of the overlap)
     """
     hab = [abs(float(v)) for v in h]
     lam = sum(hab)
@@ -85,9 +118,10 @@ def features(n: int, x, z, h, t: float, r: int) -> np.ndarray:
     supp = 0.0
     for a, xv, zv in zip(hab, x, z):
         supp += a * bin(int(xv) | int(zv)).count("1")
+    k = math.log(max(abs(error_coefficient(n, x, z, h, psi)) / (lam * lam), K_FLOOR))
     return np.array([n / 32.0, math.log(len(h)), math.log(lam), math.log(max(hab) / lam), math.log(t),
                      math.log(r), math.log(C), math.log(C) + 2.0 * math.log(t) - math.log(r), diag / lam,
-                     supp / (lam * n)], dtype=np.float64)
+                     supp / (lam * n), k, k + 2.0 * math.log(lam * t) - math.log(r)], dtype=np.float64)
 
 
 # ------------------------------------------------------------------- MLP

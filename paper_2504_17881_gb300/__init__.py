@@ -17,7 +17,12 @@ from ._lib import (PS_C64, PS_C128, PS_ERR_ARG, PS_ERR_TIMEOUT, PsError, ps_abi_
                    ps_overlap, ps_overlap_noalloc, ps_partial_length, ps_partial_stream, ps_plan_apply, ps_plan_create, ps_plan_describe,
                    ps_plan_destroy, ps_plan_export, ps_plan_get_info, ps_qdrift_stream, ps_reset_stats,
                    ps_set_state, ps_set_tuning, ps_batch_create, ps_batch_launch, ps_batch_wait, ps_batch_run,
-                   ps_batch_get_info, ps_batch_destroy, ps_batch_describe)
+                   ps_batch_get_info, ps_batch_destroy, ps_batch_describe, ps_ham_trotter_bound, ps_ham_features,
+                   ps_ham_error_coefficient,
+                   ps_trotter_stream, ps_trotter_sweep, PS_MLP_FEATURES, ps_mlp_create, ps_mlp_destroy,
+                   ps_mlp_num_params, ps_mlp_get_params, ps_mlp_set_params, ps_mlp_get_grads,
+                   ps_mlp_set_normalization, ps_mlp_get_normalization, ps_mlp_fit_normalization, ps_mlp_loss_grad,
+                   ps_mlp_adam_step, ps_mlp_train, ps_mlp_predict, ps_mlp_pick_r)
 
 __all__ = [n for n in dir(_lib) if n.startswith("ps_")] + ["StateVector", "Hamiltonian", "Plan", "Batch",
                                                               "PsError", "PS_C64", "PS_C128"]
@@ -118,11 +123,25 @@ class Hamiltonian:
 
     def __init__(self, n: int, x, z, h):
         self.n = n
+        self.L = len(h)
         self.handle = ps_ham_create(n, x, z, h)
 
     @property
     def lam(self) -> float:
         return ps_ham_lambda(self.handle)
+
+    def trotter_stream(self, t: float, r: int):
+        return ps_trotter_stream(self.handle, self.L, t, r)
+
+    def trotter_bound(self, L_D: int | None = None) -> float:
+        return ps_ham_trotter_bound(self.handle, self.L if L_D is None else L_D)
+
+    def features(self, idx, amp, t: float, r: int):
+        """Query features for first-order Trotter from the sparse state sum amp_i |idx_i>."""
+        return ps_ham_features(self.handle, idx, amp, t, r)
+
+    def error_coefficient(self, idx, amp) -> complex:
+        return ps_ham_error_coefficient(self.handle, idx, amp)
 
     def qdrift_stream(self, t: float, N: int, seed: int, first: int = 0, count: int | None = None):
         return ps_qdrift_stream(self.handle, t, N, seed, first, N - first if count is None else count)

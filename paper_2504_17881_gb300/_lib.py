@@ -65,6 +65,13 @@ class ps_batch_info(ctypes.Structure):
                 ("resident_bits", ctypes.c_int), ("single_bits", ctypes.c_int), ("graph", ctypes.c_int)]
 
 
+class ps_mlp_train_config(ctypes.Structure):
+    _fields_ = [("epochs", ctypes.c_int), ("batch", ctypes.c_int), ("lr", ctypes.c_float), ("beta1", ctypes.c_float),
+                ("beta2", ctypes.c_float), ("eps", ctypes.c_float), ("seed", ctypes.c_uint64)]
+
+
+PS_MLP_FEATURES = 12
+
 if not os.path.exists(LIB_PATH):
     raise ImportError(f"{LIB_PATH} is not built: run `python -m paper_2504_17881_gb300.build` "
                       "(or __graft_entry__.build()); there is no non-CUDA fallback")
@@ -114,6 +121,25 @@ _SIGS = {
     "ps_batch_destroy": (None, [_vp]),
     "ps_batch_describe": (_i, [_i, ctypes.POINTER(ps_run_desc), _sz, ctypes.POINTER(ps_batch_config), _i, _i,
                                ctypes.POINTER(ps_batch_info), _vp, _vp, _vp]),
+    "ps_ham_trotter_bound": (_i, [_vp, _sz, ctypes.POINTER(_d)]),
+    "ps_ham_features": (_i, [_vp, _vp, _vp, _sz, _d, _u32, _vp]),
+    "ps_ham_error_coefficient": (_i, [_vp, _vp, _vp, _sz, _vp]),
+    "ps_trotter_stream": (_i, [_vp, _d, _u32, _vp, _vp, _vp]),
+    "ps_trotter_sweep": (_i, [_vp, _vp, _vp, _d, _d, _u32, ctypes.POINTER(_u32), ctypes.POINTER(_u64), _vp]),
+    "ps_mlp_create": (_i, [_i, _u64, _vp, _pp]),
+    "ps_mlp_destroy": (None, [_vp]),
+    "ps_mlp_num_params": (_sz, [_vp]),
+    "ps_mlp_get_params": (_i, [_vp, _vp]),
+    "ps_mlp_set_params": (_i, [_vp, _vp]),
+    "ps_mlp_get_grads": (_i, [_vp, _vp]),
+    "ps_mlp_set_normalization": (_i, [_vp, _vp, _vp, ctypes.c_float, ctypes.c_float]),
+    "ps_mlp_get_normalization": (_i, [_vp, _vp, _vp, _vp, _vp]),
+    "ps_mlp_fit_normalization": (_i, [_vp, _vp, _vp, _sz]),
+    "ps_mlp_loss_grad": (_i, [_vp, _vp, _vp, _sz, ctypes.POINTER(_d)]),
+    "ps_mlp_adam_step": (_i, [_vp, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float]),
+    "ps_mlp_train": (_i, [_vp, _vp, _vp, _sz, ctypes.POINTER(ps_mlp_train_config), _vp]),
+    "ps_mlp_predict": (_i, [_vp, _vp, _sz, _vp]),
+    "ps_mlp_pick_r": (_i, [_vp, _vp, _vp, _vp, _sz, _d, _d, _d, _u32, ctypes.POINTER(_u32), _vp]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _fn = getattr(lib, _name)
@@ -420,3 +446,145 @@ def ps_batch_describe(dtype: int, runs, cfg=None, num_sms: int = 152, ctas_per_s
     d = _batch_info_dict(info)
     d.update(lane_of=lane, tile_bits_of=tb, windows_of=nw)
     return d
+
+
+# ------------------------------------------------------ learned step choice
+
+def ps_ham_trotter_bound(ham: int, L_D: int) -> float:
+    out = _d()
+    _check(lib.ps_ham_trotter_bound(ctypes.c_void_p(ham), L_D, ctypes.byref(out)))
+    return out.value
+
+
+def _sparse(idx, amp):
+    idx = _u64a(idx)
+    a = np.asarray(amp, dtype=np.complex128)
+    ri = np.ascontiguousarray(np.stack([a.real, a.imag], axis=-1).reshape(-1))
+    if len(idx) != len(a):
+        raise ValueError("idx and amp differ in length")
+    return idx, ri
+
+
+def ps_ham_features(ham: int, idx, amp, t: float, r: int) -> np.ndarray:
+    """Features of the query (t, r) from the sparse initial state sum amp_i |idx_i>."""
+    i, a = _sparse(idx, amp)
+    out = np.zeros(PS_MLP_FEATURES, dtype=np.float32)
+    _check(lib.ps_ham_features(ctypes.c_void_p(ham), _ptr(i), _ptr(a), len(i), t, r, _ptr(out)))
+    return out
+
+
+def ps_ham_error_coefficient(ham: int, idx, amp) -> complex:
+    i, a = _sparse(idx, amp)
+    out = np.zeros(2, dtype=np.float64)
+    _check(lib.ps_ham_error_coefficient(ctypes.c_void_p(ham), _ptr(i), _ptr(a), len(i), _ptr(out)))
+    return complex(out[0], out[1])
+
+
+def ps_trotter_stream(ham: int, L: int, t: float, r: int):
+    m = L * r
+    x = np.zeros(m, dtype=np.uint64)
+    z = np.zeros(m, dtype=np.uint64)
+    phi = np.zeros(m, dtype=np.float64)
+    _check(lib.ps_trotter_stream(ctypes.c_void_p(ham), t, r, _ptr(x), _ptr(z), _ptr(phi)))
+    return x, z, phi
+
+
+def ps_trotter_sweep(work: int, psi0: int, ham: int, t: float, eps: float, r_max: int):
+    """Returns (r, rotations applied, g_r)."""
+    r = _u32()
+    rot = _u64()
+    g = np.zeros(2, dtype=np.float64)
+    _check(lib.ps_trotter_sweep(ctypes.c_void_p(work), ctypes.c_void_p(psi0), ctypes.c_void_p(ham), t, eps, r_max,
+                                ctypes.byref(r), ctypes.byref(rot), _ptr(g)))
+    return int(r.value), int(rot.value), complex(g[0], g[1])
+
+
+def ps_mlp_create(n_in: int, seed: int, stream: int | None) -> int:
+    h = ctypes.c_void_p()
+    _check(lib.ps_mlp_create(n_in, seed, ctypes.c_void_p(stream or 0), ctypes.byref(h)))
+    return h.value
+
+
+def ps_mlp_destroy(m: int):
+    lib.ps_mlp_destroy(ctypes.c_void_p(m))
+
+
+def ps_mlp_num_params(m: int) -> int:
+    return int(lib.ps_mlp_num_params(ctypes.c_void_p(m)))
+
+
+def ps_mlp_get_params(m: int) -> np.ndarray:
+    out = np.zeros(ps_mlp_num_params(m), dtype=np.float32)
+    _check(lib.ps_mlp_get_params(ctypes.c_void_p(m), _ptr(out)))
+    return out
+
+
+def ps_mlp_set_params(m: int, p):
+    a = np.ascontiguousarray(np.asarray(p, dtype=np.float32))
+    if a.size != ps_mlp_num_params(m):
+        raise ValueError("wrong number of parameters")
+    _check(lib.ps_mlp_set_params(ctypes.c_void_p(m), _ptr(a)))
+
+
+def ps_mlp_get_grads(m: int) -> np.ndarray:
+    out = np.zeros(ps_mlp_num_params(m), dtype=np.float32)
+    _check(lib.ps_mlp_get_grads(ctypes.c_void_p(m), _ptr(out)))
+    return out
+
+
+def ps_mlp_set_normalization(m: int, mu, sigma, y_mu: float, y_sigma: float):
+    mu = np.ascontiguousarray(np.asarray(mu, dtype=np.float32))
+    sigma = np.ascontiguousarray(np.asarray(sigma, dtype=np.float32))
+    _check(lib.ps_mlp_set_normalization(ctypes.c_void_p(m), _ptr(mu), _ptr(sigma), y_mu, y_sigma))
+
+
+def ps_mlp_get_normalization(m: int, n_in: int):
+    mu = np.zeros(n_in, dtype=np.float32)
+    sigma = np.zeros(n_in, dtype=np.float32)
+    ym = ctypes.c_float()
+    ys = ctypes.c_float()
+    _check(lib.ps_mlp_get_normalization(ctypes.c_void_p(m), _ptr(mu), _ptr(sigma), ctypes.byref(ym),
+                                        ctypes.byref(ys)))
+    return mu, sigma, ym.value, ys.value
+
+
+def ps_mlp_fit_normalization(m: int, x, y):
+    x = np.ascontiguousarray(np.asarray(x, dtype=np.float32))
+    y = np.ascontiguousarray(np.asarray(y, dtype=np.float32))
+    _check(lib.ps_mlp_fit_normalization(ctypes.c_void_p(m), _ptr(x), _ptr(y), len(y)))
+
+
+def ps_mlp_loss_grad(m: int, x_dev: int, y_dev: int, rows: int) -> float:
+    out = _d()
+    _check(lib.ps_mlp_loss_grad(ctypes.c_void_p(m), ctypes.c_void_p(x_dev), ctypes.c_void_p(y_dev), rows,
+                                ctypes.byref(out)))
+    return out.value
+
+
+def ps_mlp_adam_step(m: int, lr: float, beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8):
+    _check(lib.ps_mlp_adam_step(ctypes.c_void_p(m), lr, beta1, beta2, eps))
+
+
+def ps_mlp_train(m: int, x_dev: int, y_dev: int, rows: int, cfg=None) -> np.ndarray:
+    c = cfg if isinstance(cfg, ps_mlp_train_config) else ps_mlp_train_config(**(cfg or {}))
+    epochs = c.epochs or 200
+    out = np.zeros(epochs, dtype=np.float32)
+    _check(lib.ps_mlp_train(ctypes.c_void_p(m), ctypes.c_void_p(x_dev), ctypes.c_void_p(y_dev), rows,
+                            ctypes.byref(c), _ptr(out)))
+    return out
+
+
+def ps_mlp_predict(m: int, x_dev: int, rows: int, y_dev: int):
+    _check(lib.ps_mlp_predict(ctypes.c_void_p(m), ctypes.c_void_p(x_dev), rows, ctypes.c_void_p(y_dev)))
+
+
+def ps_mlp_pick_r(m: int, ham: int, idx, amp, t: float, eps: float, margin: float, r_max: int):
+    """Returns (r, predictions for r = 1..r_max); r = 0 when none qualifies."""
+    i, a = _sparse(idx, amp)
+    r = _u32()
+    pred = np.zeros(r_max, dtype=np.float32)
+    rc = lib.ps_mlp_pick_r(ctypes.c_void_p(m), ctypes.c_void_p(ham), _ptr(i), _ptr(a), len(i), t, eps, margin, r_max,
+                           ctypes.byref(r), _ptr(pred))
+    if rc not in (PS_OK, PS_ERR_UNSUPPORTED):
+        _check(rc)
+    return int(r.value), pred

@@ -112,9 +112,6 @@ struct ps_state {
     std::vector<cudaEvent_t> event_pool;
 };
 
-struct ps_ham {
-    Ham H;
-};
 
 struct ps_plan {
     Plan plan;  // host copy; every launch passes its window by value

@@ -192,6 +192,44 @@ constexpr size_t kRecBytesC64 = 160, kRecBytesC128 = 288;
 constexpr int kBatchG = 3;       // group bits of the batched kernel
 constexpr int kLaneStrideWords = 32;
 
+// ------------------------------------------------------ learned step choice
+constexpr int kMlpWidth = 128;     // units of each of the three hidden layers
+constexpr int kMlpMaxIn = 16;      // most input features
+constexpr int kMlpFeatures = 12;   // features of a (Hamiltonian, t, r, initial state) query
+
+struct MlpNorm {
+    float mu[kMlpMaxIn], inv_sigma[kMlpMaxIn];
+    float y_mu, y_inv_sigma;
+};
+
+int mlp_num_params(int n_in);
+int mlp_prepare();
+int mlp_launch_init(float *P, int n_in, uint64_t seed, void *stream);
+int mlp_launch_standardize(const float *x, const float *y, int rows, int n_in, const MlpNorm &nm, float *xs,
+                           float *ys, void *stream);
+int mlp_launch_forward(const float *P, const float *xs, const int *idx, int rows, int n_in, float *acts, float *out,
+                       int denorm, float y_mu, float y_sigma, void *stream);
+int mlp_launch_backward(const float *P, const float *ts, const int *idx, int rows, int n_in, float inv_B,
+                        const float *acts, const float *out, float *deltas, float *loss_part, void *stream);
+int mlp_launch_wgrad(const float *xs, const int *idx, int rows, int n_in, const float *acts, const float *deltas,
+                     float *G, void *stream);
+int mlp_launch_adam(float *P, const float *G, float *M, float *V, int n, float lr, float beta1, float beta2,
+                    float eps, unsigned *count, void *stream);
+
+// A sparse initial state: basis states and their amplitudes.
+struct SparseState {
+    std::vector<uint64_t> idx;
+    std::vector<double> re, im;
+};
+
+// Features of "first-order Trotter, r steps to time t from psi" for a
+// Hamiltonian whose bound (every term deterministic) is C and whose
+// leading-order error coefficient on psi has modulus K_abs.
+void query_features(const Ham &H, double C, double K_abs, double t, uint32_t r, float *out);
+// The same for a Hamiltonian handle (bound and coefficient cached per state).
+int ham_query_features(ps_ham *ham, const uint64_t *idx, const double *amp, size_t ndet, double t, uint32_t r,
+                       float *out);
+
 // Kernel parameters of one tile window, from the host copy of a plan.
 void fill_tile_params(const Plan &p, const WinDesc &w, TileParams &tp);
 
@@ -206,3 +244,14 @@ int reduce_blocks();
 int prepare_kernels(int dtype);
 
 }  // namespace ps
+
+// A Hamiltonian handle (include/ps.h): the term list and, once computed,
+// its Trotter-error bound with every term deterministic.
+struct ps_ham {
+    ps::Ham H;
+    double bound_full = -1.0;
+    // the error coefficient of the last state it was computed for
+    ps::SparseState k_state;
+    double k_re = 0.0, k_im = 0.0;
+    bool k_valid = false;
+};

@@ -1,0 +1,267 @@
+// Host side of the learned step choice: the analytic Trotter-error bound,
+// the feature vector of a (Hamiltonian, t, r) query, the Trotter stream
+// export, and the plain doubling sweep that the learned choice replaces and
+// that judges it.  See include/ps.h.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <sstream>
+#include <unordered_map>
+#include <unordered_set>
+#include <vector>
+
+#include "ps_internal.h"
+#include "ps_sample.h"
+
+namespace ps {
+namespace {
+
+int lfail(int code, const std::string &msg) {
+    set_error(msg);
+    return code;
+}
+
+// Pauli strings (x1, z1) and (x2, z2) anticommute iff their symplectic
+// product popc(x1 & z2) + popc(z1 & x2) is odd.
+inline bool anticommute(uint64_t x1, uint64_t z1, uint64_t x2, uint64_t z2) {
+    return (__builtin_popcountll((x1 & z2) ^ (z1 & x2)) & 1) != 0;
+}
+
+// Bound on the Trotter-error prefactor of the partially randomised
+// decomposition (Methods, "Data analysis"): the deterministic part D = the
+// first L_D terms by decreasing |h|, lambda_R the one-norm of the rest:
+//   4 sum_{l in D} |h_l| sum_{k in D anticommuting with l} |h_k|
+//     + lambda_R (lambda - lambda_R)^2 + (lambda - lambda_R) lambda_R^2.
+double trotter_bound(const Ham &H, size_t L_D) {
+    std::vector<size_t> det, rest;
+    split_terms(H, L_D, det, rest);
+    double lam = 0.0, lam_r = 0.0;
+    for (double v : H.h) lam += std::fabs(v);
+    for (size_t k : rest) lam_r += std::fabs(H.h[k]);
+    double s = 0.0;
+    for (size_t l : det) {
+        double acc = 0.0;
+        for (size_t k : det)
+            if (anticommute(H.x[l], H.z[l], H.x[k], H.z[k])) acc += std::fabs(H.h[k]);
+        s += std::fabs(H.h[l]) * acc;
+    }
+    const double lam_d = lam - lam_r;
+    return 4.0 * s + lam_r * lam_d * lam_d + lam_d * lam_r * lam_r;
+}
+
+double full_bound(ps_ham *ham) {
+    if (ham->bound_full < 0.0) ham->bound_full = trotter_bound(ham->H, ham->H.h.size());
+    return ham->bound_full;
+}
+
+// Coefficient of P|b> = i^{popc(x&z)} (-1)^{popc(b&z)} |b ^ x> as (re, im).
+inline void pauli_coef(uint64_t x, uint64_t z, uint64_t b, double &cr, double &ci) {
+    const int y = __builtin_popcountll(x & z) & 3;
+    const double s = (__builtin_popcountll(b & z) & 1) ? -1.0 : 1.0;
+    // i^y: 1, i, -1, -i
+    cr = (y == 0) ? s : (y == 2) ? -s : 0.0;
+    ci = (y == 1) ? s : (y == 3) ? -s : 0.0;
+}
+
+// K = sum over term pairs k < l (k applied first) that anticommute of
+// h_l h_k <psi|P_l P_k|psi>: one first-order Trotter step of size delta is
+// exp(i delta H - (delta^2 / 2) sum_{l>k} h_l h_k [P_l, P_k] + ...) and
+// [P_l, P_k] = 2 P_l P_k for anticommuting strings, so for small t the
+// overlap error is g_r - g = -(t^2 / r) K + O(t^3 / r).  <psi|P_l P_k|psi>
+// = sum_b conj(psi(b ^ x_k ^ x_l)) c_l(b ^ x_k) c_k(b) psi(b) is nonzero only
+// when x_k ^ x_l is a difference of two basis states of psi.
+void error_coefficient(const Ham &H, const SparseState &st, double &Kr, double &Ki) {
+    std::unordered_map<uint64_t, size_t> pos;
+    for (size_t i = 0; i < st.idx.size(); ++i) pos[st.idx[i]] = i;
+    std::unordered_set<uint64_t> diff;
+    for (uint64_t a : st.idx)
+        for (uint64_t b : st.idx) diff.insert(a ^ b);
+    Kr = Ki = 0.0;
+    const size_t L = H.h.size();
+    for (size_t k = 0; k < L; ++k) {
+        for (size_t l = k + 1; l < L; ++l) {
+            const uint64_t xkl = H.x[k] ^ H.x[l];
+            if (!diff.count(xkl) || !anticommute(H.x[l], H.z[l], H.x[k], H.z[k])) continue;
+            double er = 0.0, ei = 0.0;  // <psi|P_l P_k|psi>
+            for (size_t i = 0; i < st.idx.size(); ++i) {
+                const uint64_t b = st.idx[i];
+                const auto it = pos.find(b ^ xkl);
+                if (it == pos.end()) continue;
+                double c1r, c1i, c2r, c2i;
+                pauli_coef(H.x[k], H.z[k], b, c1r, c1i);
+                pauli_coef(H.x[l], H.z[l], b ^ H.x[k], c2r, c2i);
+                // c = c2 c1 psi(b); then conj(psi(a)) c
+                const double cr = c2r * c1r - c2i * c1i, ci = c2r * c1i + c2i * c1r;
+                const double pr = cr * st.re[i] - ci * st.im[i], pi = cr * st.im[i] + ci * st.re[i];
+                const size_t j = it->second;
+                er += st.re[j] * pr + st.im[j] * pi;
+                ei += st.re[j] * pi - st.im[j] * pr;
+            }
+            Kr += H.h[l] * H.h[k] * er;
+            Ki += H.h[l] * H.h[k] * ei;
+        }
+    }
+}
+
+int read_state(const Ham &H, const uint64_t *idx, const double *amp, size_t ndet, SparseState &st) {
+    if (ndet == 0 || !idx || !amp) return lfail(PS_ERR_ARG, "the initial state needs at least one basis state");
+    if (ndet > 65536) return lfail(PS_ERR_ARG, "at most 65536 basis states in a sparse initial state");
+    st.idx.assign(idx, idx + ndet);
+    st.re.resize(ndet);
+    st.im.resize(ndet);
+    std::unordered_set<uint64_t> seen;
+    for (size_t i = 0; i < ndet; ++i) {
+        if (H.n < 64 && (idx[i] >> H.n)) return lfail(PS_ERR_ARG, "basis state index >= 2^n");
+        if (!seen.insert(idx[i]).second) return lfail(PS_ERR_ARG, "repeated basis state in the initial state");
+        st.re[i] = amp[2 * i];
+        st.im[i] = amp[2 * i + 1];
+        if (!std::isfinite(st.re[i]) || !std::isfinite(st.im[i])) return lfail(PS_ERR_ARG, "non-finite amplitude");
+    }
+    return PS_OK;
+}
+
+bool same_state(const SparseState &a, const SparseState &b) {
+    return a.idx == b.idx && a.re == b.re && a.im == b.im;
+}
+
+}  // namespace
+
+// Features of "first-order Trotter with r steps to time t from psi"
+// (PS_MLP_FEATURES): n / 32, log L, log lambda, log(max|h| / lambda), log t,
+// log r, log C, log(C t^2 / r), diagonal weight fraction, mean support
+// fraction, log max(|K| / lambda^2, 1e-12), and that plus log(lambda^2 t^2 / r);
+// C the bound above for L_D = L, K the error coefficient on psi.
+void query_features(const Ham &H, double C, double K_abs, double t, uint32_t r, float *out) {
+    double lam = 0.0, hmax = 0.0, diag = 0.0, supp = 0.0;
+    for (size_t l = 0; l < H.h.size(); ++l) {
+        const double a = std::fabs(H.h[l]);
+        lam += a;
+        hmax = std::max(hmax, a);
+        if (H.x[l] == 0) diag += a;
+        supp += a * (double)__builtin_popcountll(H.x[l] | H.z[l]);
+    }
+    const double logC = std::log(C);
+    out[0] = (float)(H.n / 32.0);
+    out[1] = (float)std::log((double)H.h.size());
+    out[2] = (float)std::log(lam);
+    out[3] = (float)std::log(hmax / lam);
+    out[4] = (float)std::log(t);
+    out[5] = (float)std::log((double)r);
+    out[6] = (float)logC;
+    out[7] = (float)(logC + 2.0 * std::log(t) - std::log((double)r));
+    out[8] = (float)(diag / lam);
+    out[9] = (float)(supp / (lam * H.n));
+    const double k = std::log(std::max(K_abs / (lam * lam), 1e-12));
+    out[10] = (float)k;
+    out[11] = (float)(k + 2.0 * std::log(lam * t) - std::log((double)r));
+}
+
+static int ham_coefficient(ps_ham *ham, const uint64_t *idx, const double *amp, size_t ndet) {
+    SparseState st;
+    if (int rc = read_state(ham->H, idx, amp, ndet, st)) return rc;
+    if (!ham->k_valid || !same_state(st, ham->k_state)) {
+        error_coefficient(ham->H, st, ham->k_re, ham->k_im);
+        ham->k_state = std::move(st);
+        ham->k_valid = true;
+    }
+    return PS_OK;
+}
+
+int ham_query_features(ps_ham *ham, const uint64_t *idx, const double *amp, size_t ndet, double t, uint32_t r,
+                       float *out) {
+    if (!ham) return lfail(PS_ERR_ARG, "null Hamiltonian");
+    if (!out) return lfail(PS_ERR_ARG, "null output pointer");
+    if (!(t > 0.0) || !std::isfinite(t)) return lfail(PS_ERR_ARG, "t must be positive and finite");
+    if (r == 0) return lfail(PS_ERR_ARG, "r must be >= 1");
+    const double C = full_bound(ham);
+    double lam = 0.0;
+    for (double v : ham->H.h) lam += std::fabs(v);
+    if (!(lam > 0.0)) return lfail(PS_ERR_ARG, "Hamiltonian with zero one-norm");
+    if (!(C > 0.0)) return lfail(PS_ERR_ARG, "Hamiltonian whose terms all commute (bound 0): no Trotter error");
+    if (int rc = ham_coefficient(ham, idx, amp, ndet)) return rc;
+    query_features(ham->H, C, std::hypot(ham->k_re, ham->k_im), t, r, out);
+    return PS_OK;
+}
+
+}  // namespace ps
+
+using namespace ps;
+
+extern "C" {
+
+int ps_ham_trotter_bound(const ps_ham *ham, size_t L_D, double *out) {
+    if (!ham || !out) return lfail(PS_ERR_ARG, "null argument");
+    if (L_D > ham->H.h.size()) return lfail(PS_ERR_ARG, "L_D exceeds the number of terms");
+    *out = trotter_bound(ham->H, L_D);
+    return PS_OK;
+}
+
+int ps_ham_features(ps_ham *ham, const uint64_t *idx, const double *amp, size_t ndet, double t, uint32_t r,
+                    float *out) {
+    return ham_query_features(ham, idx, amp, ndet, t, r, out);
+}
+
+int ps_ham_error_coefficient(ps_ham *ham, const uint64_t *idx, const double *amp, size_t ndet, double *out) {
+    if (!ham || !out) return lfail(PS_ERR_ARG, "null argument");
+    if (int rc = ham_coefficient(ham, idx, amp, ndet)) return rc;
+    out[0] = ham->k_re;
+    out[1] = ham->k_im;
+    return PS_OK;
+}
+
+int ps_trotter_stream(const ps_ham *ham, double t, uint32_t r, uint64_t *x_out, uint64_t *z_out, double *phi_out) {
+    if (!ham) return lfail(PS_ERR_ARG, "null Hamiltonian");
+    if (r == 0) return lfail(PS_ERR_ARG, "r must be >= 1");
+    Stream s;
+    trotter_stream(ham->H, t, r, s);
+    if (s.size() && (!x_out || !z_out || !phi_out)) return lfail(PS_ERR_ARG, "null output array");
+    std::copy(s.x.begin(), s.x.end(), x_out);
+    std::copy(s.z.begin(), s.z.end(), z_out);
+    std::copy(s.phi.begin(), s.phi.end(), phi_out);
+    return PS_OK;
+}
+
+int ps_trotter_sweep(ps_state *work, const ps_state *psi0, const ps_ham *ham, double t, double eps, uint32_t r_max,
+                     uint32_t *r_out, uint64_t *rotations_out, double *g_out) {
+    if (!work || !psi0 || !ham || !r_out) return lfail(PS_ERR_ARG, "null argument");
+    if (!(eps > 0.0)) return lfail(PS_ERR_ARG, "eps must be positive");
+    if (r_max == 0) return lfail(PS_ERR_ARG, "r_max must be >= 1");
+    // g_r for r = 1, 2, 4, ...; stop at the first r with 2 |g_r - g_2r| <= eps
+    // (first order: g_r - g_exact ~ a / r, so the error of g_r is about
+    // 2 |g_r - g_2r|)
+    uint64_t spent = 0;
+    double g_prev[2] = {0.0, 0.0};
+    uint32_t r_prev = 0;
+    const uint64_t L = ham->H.h.size();
+    for (uint32_t r = 1;; r *= 2) {
+        if (int rc = ps_copy_state(work, psi0)) return rc;
+        if (int rc = ps_evolve_trotter(work, ham, t, r)) return rc;
+        double g[2];
+        if (int rc = ps_overlap(psi0, work, g)) return rc;
+        spent += L * (uint64_t)r;
+        if (r_prev) {
+            const double d = std::hypot(g[0] - g_prev[0], g[1] - g_prev[1]);
+            if (2.0 * d <= eps) {
+                *r_out = r_prev;
+                if (rotations_out) *rotations_out = spent;
+                if (g_out) {
+                    g_out[0] = g_prev[0];
+                    g_out[1] = g_prev[1];
+                }
+                return PS_OK;
+            }
+        }
+        g_prev[0] = g[0];
+        g_prev[1] = g[1];
+        r_prev = r;
+        if ((uint64_t)r * 2 > (uint64_t)r_max) break;
+    }
+    *r_out = 0;
+    if (rotations_out) *rotations_out = spent;
+    std::ostringstream os;
+    os << "doubling sweep did not reach eps = " << eps << " by r = " << r_prev;
+    return lfail(PS_ERR_UNSUPPORTED, os.str());
+}
+
+}  // extern "C"

@@ -78,7 +78,7 @@ int qdrift_stream(const Ham &H, double t, uint64_t N, uint64_t seed, uint64_t fi
     return PS_OK;
 }
 
-static void split(const Ham &H, size_t L_D, std::vector<size_t> &det, std::vector<size_t> &rest) {
+void split_terms(const Ham &H, size_t L_D, std::vector<size_t> &det, std::vector<size_t> &rest) {
     const size_t L = H.h.size();
     std::vector<size_t> order(L);
     std::iota(order.begin(), order.end(), 0);
@@ -93,7 +93,7 @@ static void split(const Ham &H, size_t L_D, std::vector<size_t> &det, std::vecto
 
 uint64_t partial_length(const Ham &H, size_t L_D, uint32_t r, uint64_t Ns) {
     std::vector<size_t> det, rest;
-    split(H, L_D, det, rest);
+    split_terms(H, L_D, det, rest);
     double lam_r = 0.0;
     for (size_t l : rest) lam_r += std::fabs(H.h[l]);
     const bool sample = !rest.empty() && Ns > 0 && lam_r > 0.0;
@@ -102,7 +102,7 @@ uint64_t partial_length(const Ham &H, size_t L_D, uint32_t r, uint64_t Ns) {
 
 void partial_stream(const Ham &H, size_t L_D, double t, uint32_t r, uint64_t Ns, uint64_t seed, Stream &out) {
     std::vector<size_t> det, rest;
-    split(H, L_D, det, rest);
+    split_terms(H, L_D, det, rest);
     std::vector<double> cdf = running_abs(H.h, rest);
     const double lam_r = rest.empty() ? 0.0 : cdf.back();
     const bool sample = !rest.empty() && Ns > 0 && lam_r > 0.0;

@@ -21,6 +21,9 @@ struct Stream {
 };
 
 double ham_lambda(const Ham &H);
+// The first L_D terms by decreasing |h| (ties in input order) and the rest,
+// each list in input order.
+void split_terms(const Ham &H, size_t L_D, std::vector<size_t> &det, std::vector<size_t> &rest);
 void trotter_stream(const Ham &H, double t, uint32_t r, Stream &out);
 int qdrift_stream(const Ham &H, double t, uint64_t N, uint64_t seed, uint64_t first, uint64_t count, uint64_t *xo,
                   uint64_t *zo, double *po, std::string *err);

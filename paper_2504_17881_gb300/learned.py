@@ -1,0 +1,266 @@
+"""Learned Trotter step choice (the network, its training data, the r pick).
+
+A step count r for first-order Trotter to time t is good when the error of
+the overlap, eps(H, t, r) = |g_r(t) - g(t)| with g(t) = <psi|exp(itH)|psi>,
+is at most the target (the paper works at eps = 0.001, Methods).  The plain
+way to find it is the doubling sweep (``ps_trotter_sweep``): r = 1, 2, 4, ...
+until 2 |g_r - g_2r| <= eps, paying for every run on the way.  The learned
+way predicts log eps(H, t, r) from twelve features of the query
+(``ps_ham_features``) with a small network trained on errors this simulator
+measures, and runs only the r it picks; the sweep stays as the fallback and
+the judge.
+
+Training rows come from the batched engine: for every Hamiltonian and time,
+Trotter runs at r = 1, 2, ..., 64 and at 128 share one persistent launch with
+many other (H, t) pairs; g is extrapolated from r = 32, 64, 128 by
+three-point Richardson extrapolation in 1/r (first order: g_r = g + a/r +
+b/r^2 + ...), and eps = |g_r - g|.
+
+All arithmetic runs in libps (features and bound on the host in C++, the
+network's forward, backward and Adam steps in CUDA kernels); this module
+arranges the calls.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+from . import PS_MLP_FEATURES, Batch, Hamiltonian, StateVector, _lib, ps_trotter_sweep
+
+TIMES16 = tuple(0.1 * 2.0 ** (j / 3.0) for j in range(16))  # 0.1 .. 3.2
+R_VALUES = (1, 2, 4, 8, 16, 32, 64)
+R_EXTRA = 128
+EPS_FLOOR = 1e-12
+
+
+def richardson3(g32: complex, g64: complex, g128: complex) -> complex:
+    """The r -> infinity limit of g_r = g + a/r + b/r^2 from r = R, 2R, 4R."""
+    return (8.0 * g128 - 6.0 * g64 + g32) / 3.0
+
+
+def initial_state(n: int, seed: int, dtype, device):
+    """The 8-determinant guiding state on the device (Methods: a few leading
+    determinants stand in for the ground state)."""
+    import torch
+
+    from . import inputs
+    idx, amp = inputs.determinant_state(n, seed=seed)
+    t = torch.zeros(1 << n, dtype=dtype, device=device)
+    t[torch.as_tensor(idx.astype(np.int64), device=device)] = torch.as_tensor(amp, device=device).to(dtype)
+    return t
+
+
+class Problem:
+    """One Hamiltonian with its initial state (8 determinants from a seed)."""
+
+    def __init__(self, n: int, x, z, h, psi_seed: int):
+        from . import inputs
+        self.n, self.x, self.z, self.h = n, np.asarray(x, np.uint64), np.asarray(z, np.uint64), np.asarray(h)
+        self.psi_seed = psi_seed
+        self.ham = Hamiltonian(n, self.x, self.z, self.h)
+        self.det_idx, self.det_amp = inputs.determinant_state(n, seed=psi_seed)
+
+    def features(self, t: float, r: int):
+        return self.ham.features(self.det_idx, self.det_amp, t, r)
+
+    @property
+    def L(self) -> int:
+        return len(self.h)
+
+
+def synthetic_problems(count: int, seed: int, n_range=(14, 22), L_range=(200, 2000), lam_range=None):
+    """Seeded JW-like Hamiltonians: n uniform in n_range, L uniform in
+    L_range, one-norm uniform in lam_range (default: the generator's
+    L-dependent one-norm)."""
+    from . import inputs
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        n = int(rng.integers(n_range[0], n_range[1] + 1))
+        L = int(rng.integers(L_range[0], L_range[1] + 1))
+        lam = None if lam_range is None else float(rng.uniform(lam_range[0], lam_range[1]))
+        x, z, h = inputs.jw_hamiltonian(n, L, seed=seed * 7919 + i, lam=lam)
+        out.append(Problem(n, x, z, h, psi_seed=seed * 7919 + i))
+    return out
+
+
+def overlaps_by_batch(problems, times, r_values, dtype=None, cfg=None, max_rotations: int = 40_000_000,
+                      device="cuda"):
+    """g[p][t][r] = <psi_p|U_r(t)|psi_p> for every problem, time and r, from
+    batched launches of at most max_rotations rotations each."""
+    import torch
+    dtype = torch.complex64 if dtype is None else dtype
+    jobs = [(pi, ti, r) for pi in range(len(problems)) for ti in range(len(times)) for r in r_values]
+    g = {}
+    start = 0
+    while start < len(jobs):
+        chunk, rot = [], 0
+        while start < len(jobs):
+            pi, ti, r = jobs[start]
+            cost = problems[pi].L * r
+            if chunk and rot + cost > max_rotations:
+                break
+            chunk.append(jobs[start])
+            rot += cost
+            start += 1
+        psi0 = {}
+        runs = []
+        for pi, ti, r in chunk:
+            p = problems[pi]
+            if pi not in psi0:
+                psi0[pi] = initial_state(p.n, p.psi_seed, dtype, device)
+            x, z, phi = p.ham.trotter_stream(times[ti], r)
+            runs.append(dict(n=p.n, x=x, z=z, phi=phi, psi0=psi0[pi]))
+        b = Batch(runs, dtype=dtype, cfg=cfg, device=device)
+        res = b.run()
+        b.close()
+        for (pi, ti, r), v in zip(chunk, res):
+            g[(pi, ti, r)] = complex(v)
+        del runs, b, psi0
+    return g
+
+
+def training_rows(problems, times=TIMES16, r_values=R_VALUES, dtype=None, cfg=None, max_rotations=40_000_000):
+    """(features [rows x 10] float32, log eps [rows] float32, info) for every
+    problem, time and r in r_values, errors against the Richardson limit of
+    r = 32, 64, 128.  The runs are complex128 by default: the errors that
+    decide r sit near 1e-3 and below, where complex64 rounding of a
+    10^5-rotation run (about 1e-5 in the overlap) would blur them."""
+    import torch
+    dtype = torch.complex128 if dtype is None else dtype
+    rs = tuple(sorted(set(r_values) | {32, 64, R_EXTRA}))
+    g = overlaps_by_batch(problems, times, rs, dtype=dtype, cfg=cfg, max_rotations=max_rotations)
+    X, y, info = [], [], []
+    for pi, p in enumerate(problems):
+        for ti, t in enumerate(times):
+            g_lim = richardson3(g[(pi, ti, 32)], g[(pi, ti, 64)], g[(pi, ti, R_EXTRA)])
+            for r in r_values:
+                eps = abs(g[(pi, ti, r)] - g_lim)
+                X.append(p.features(t, r))
+                y.append(math.log(max(eps, EPS_FLOOR)))
+                info.append((pi, ti, r, eps))
+    return np.asarray(X, np.float32), np.asarray(y, np.float32), info
+
+
+class StepPredictor:
+    """The FP32 network (three tanh layers of 128) on the current device."""
+
+    def __init__(self, seed: int = 0, stream=None):
+        import torch
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.handle = _lib.ps_mlp_create(PS_MLP_FEATURES, seed, self.stream.cuda_stream)
+        self.margin = 0.0
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _lib.ps_mlp_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def params(self) -> np.ndarray:
+        return _lib.ps_mlp_get_params(self.handle)
+
+    def set_params(self, p):
+        _lib.ps_mlp_set_params(self.handle, p)
+
+    def normalization(self):
+        return _lib.ps_mlp_get_normalization(self.handle, PS_MLP_FEATURES)
+
+    def set_normalization(self, mu, sigma, y_mu, y_sigma):
+        _lib.ps_mlp_set_normalization(self.handle, mu, sigma, y_mu, y_sigma)
+
+    def fit(self, X, y, epochs=300, batch=256, lr=1e-3, seed=0):
+        """Standardise on (X, y) and train; returns the loss of every epoch."""
+        import torch
+        X = np.ascontiguousarray(np.asarray(X, np.float32))
+        y = np.ascontiguousarray(np.asarray(y, np.float32))
+        _lib.ps_mlp_fit_normalization(self.handle, X, y)
+        xd = torch.as_tensor(X).cuda()
+        yd = torch.as_tensor(y).cuda()
+        losses = _lib.ps_mlp_train(self.handle, xd.data_ptr(), yd.data_ptr(), len(y),
+                                   dict(epochs=epochs, batch=batch, lr=lr, seed=seed))
+        torch.cuda.synchronize()
+        return losses
+
+    def calibrate_margin(self, X_val, y_val, quantile: float = 0.8) -> float:
+        """Margin for pick_r: the given quantile of the held-out residuals
+        log eps - prediction (at least 0), so that the prediction plus the
+        margin bounds the error in about that fraction of cases."""
+        resid = np.asarray(y_val, np.float64) - self.predict(X_val)
+        self.margin = max(0.0, float(np.quantile(resid, quantile)))
+        return self.margin
+
+    def predict(self, X) -> np.ndarray:
+        import torch
+        X = np.ascontiguousarray(np.asarray(X, np.float32))
+        xd = torch.as_tensor(X).cuda()
+        yd = torch.empty(len(X), dtype=torch.float32, device="cuda")
+        _lib.ps_mlp_predict(self.handle, xd.data_ptr(), len(X), yd.data_ptr())
+        return yd.cpu().numpy()
+
+    def pick_r(self, problem: Problem, t: float, eps: float = 1e-3, margin: float | None = None, r_max: int = 4096):
+        """(r, predictions for r = 1..r_max); r = 0 when no r <= r_max
+        qualifies.  The margin defaults to the calibrated one."""
+        m = self.margin if margin is None else margin
+        return _lib.ps_mlp_pick_r(self.handle, problem.ham.handle, problem.det_idx, problem.det_amp, t, eps, m, r_max)
+
+    def save(self, path: str):
+        mu, sigma, ym, ys = self.normalization()
+        np.savez(path, params=self.params(), mu=mu, sigma=sigma, y_mu=ym, y_sigma=ys, margin=self.margin)
+
+    def load(self, path: str):
+        d = np.load(path)
+        self.set_params(d["params"])
+        self.set_normalization(d["mu"], d["sigma"], float(d["y_mu"]), float(d["y_sigma"]))
+        self.margin = float(d["margin"])
+
+
+def sweep(problem: Problem, t: float, eps: float = 1e-3, r_max: int = 4096, dtype=None):
+    """The plain doubling sweep on one GPU state: (r, rotations applied, g_r)."""
+    import torch
+    dtype = torch.complex64 if dtype is None else dtype
+    psi0 = StateVector(problem.n, tensor=initial_state(problem.n, problem.psi_seed, dtype, "cuda"))
+    work = StateVector(problem.n, dtype=dtype)
+    try:
+        return ps_trotter_sweep(work.handle, psi0.handle, problem.ham.handle, t, eps, r_max)
+    finally:
+        work.close()
+        psi0.close()
+
+
+def bound_r(problem: Problem, t: float, eps: float = 1e-3) -> int:
+    """Step count from the analytic bound: eps = C delta^2 with delta = t / r
+    (the paper's error model), so r = ceil(t sqrt(C / eps))."""
+    C = problem.ham.trotter_bound()
+    return max(1, int(math.ceil(t * math.sqrt(C / eps))))
+
+
+def run_error(problem: Problem, t: float, r: int, g_ref: complex, dtype=None) -> float:
+    """|g_r - g_ref| for one Trotter run on the GPU."""
+    import torch
+    dtype = torch.complex64 if dtype is None else dtype
+    psi0 = StateVector(problem.n, tensor=initial_state(problem.n, problem.psi_seed, dtype, "cuda"))
+    work = StateVector(problem.n, dtype=dtype)
+    try:
+        work.copy_from(psi0)
+        work.evolve_trotter(problem.ham, t, r)
+        return abs(work.overlap(psi0) - g_ref)
+    finally:
+        work.close()
+        psi0.close()
+
+
+def reference_overlap(problem: Problem, t: float, R: int = 256, dtype=None) -> complex:
+    """Richardson limit from r = R, 2R, 4R (one batched launch)."""
+    g = overlaps_by_batch([problem], [t], (R, 2 * R, 4 * R), dtype=dtype)
+    return richardson3(g[(0, 0, R)], g[(0, 0, 2 * R)], g[(0, 0, 4 * R)])
+
+
+__all__ = ["StepPredictor", "Problem", "synthetic_problems", "training_rows", "overlaps_by_batch", "sweep",
+           "bound_r", "run_error", "reference_overlap", "richardson3", "TIMES16", "R_VALUES"]

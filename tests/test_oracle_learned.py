@@ -62,16 +62,51 @@ def test_bound_closed_forms():
 
 
 def test_features_hand_example():
-    # n = 2: 0.5 X1, -0.25 Z1 Z2, 0.25 Y2
+    # n = 2: 0.5 X1, -0.25 Z1 Z2, 0.25 Y2; psi = |00>
     n, x, z, h = 2, [1, 0, 2], [0, 3, 2], [0.5, -0.25, 0.25]
+    psi = np.zeros(4, dtype=complex)
+    psi[0] = 1.0
     t, r = 0.8, 4
-    f = L.features(n, x, z, h, t, r)
+    f = L.features(n, x, z, h, t, r, psi)
     lam = 1.0
     # anticommuting pairs: X1 with Z1Z2 (qubit 1: X vs Z), Z1Z2 with Y2 (qubit 2: Z vs Y); X1 and Y2 commute
     C = 4 * (0.5 * 0.25 + 0.25 * (0.5 + 0.25) + 0.25 * 0.25)
+    # K on |00>: pair (X1, Z1Z2): h2 h1 <00|Z1Z2 X1|00> = 0 (X1 flips qubit 1);
+    # pair (Z1Z2, Y2): h3 h2 <00|Y2 Z1Z2|00> = 0 (Y2 flips qubit 2)
     expect = [2 / 32, math.log(3), math.log(lam), math.log(0.5), math.log(t), math.log(r), math.log(C),
-              math.log(C * t * t / r), 0.25, (0.5 * 1 + 0.25 * 2 + 0.25 * 1) / (lam * 2)]
+              math.log(C * t * t / r), 0.25, (0.5 * 1 + 0.25 * 2 + 0.25 * 1) / (lam * 2), math.log(L.K_FLOOR),
+              math.log(L.K_FLOOR) + 2 * math.log(t) - math.log(r)]
     assert np.allclose(f, expect, rtol=1e-14, atol=1e-15)
+
+
+def test_error_coefficient_dense_and_small_time_limit():
+    """K against dense commutators, and g_r - g -> -(t^2 / r) K as t -> 0
+    (first-order Trotter against the exact exponential of the dense H)."""
+    import scipy.linalg
+    rng = np.random.default_rng(4)
+    n = 3
+    x = [1, 3, 6, 2, 5, 0]
+    z = [0, 1, 6, 3, 4, 5]
+    h = list(rng.normal(size=len(x)))
+    psi = rng.normal(size=8) + 1j * rng.normal(size=8)
+    psi /= np.linalg.norm(psi)
+    P = [dense(n, xv, zv) for xv, zv in zip(x, z)]
+    Kd = 0j
+    for k in range(len(h)):
+        for l in range(k + 1, len(h)):
+            Kd += h[l] * h[k] * np.vdot(psi, (P[l] @ P[k] - P[k] @ P[l]) @ psi) / 2
+    K = L.error_coefficient(n, x, z, h, psi)
+    assert abs(K - Kd) < 1e-13
+    H = sum(hv * Pm for hv, Pm in zip(h, P))
+    for r in (1, 3):
+        t = 2e-3
+        step = np.eye(8, dtype=complex)
+        for hv, Pm in zip(h, P):
+            step = scipy.linalg.expm(1j * (t / r) * hv * Pm) @ step
+        Ur = np.linalg.matrix_power(step, r)
+        g_r = np.vdot(psi, Ur @ psi)
+        g = np.vdot(psi, scipy.linalg.expm(1j * t * H) @ psi)
+        assert abs((g_r - g) * r / t ** 2 + K) < 2e-2 * max(1.0, abs(K))
 
 
 def rand_params(n_in, width, seed, scale=0.6):
