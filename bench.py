@@ -66,12 +66,14 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
-    ap.add_argument("--workload", choices=["qdrift30", "batched"], default="qdrift30",
+    ap.add_argument("--workload", choices=["qdrift30", "batched", "learned"], default="qdrift30",
                     help="batched: 512 independent qDRIFT / partially randomised runs, n 14..22, in one "
                          "persistent launch (reported on its own JSON line)")
     ap.add_argument("--batch-runs", type=int, default=BATCH_RUNS)
     ap.add_argument("--no-sequential", action="store_true", help="batched: skip the one-run-at-a-time comparison")
     ap.add_argument("--no-autotune", action="store_true", help="batched: default lane size and tile bits")
+    ap.add_argument("--train-problems", type=int, default=96, help="learned: training Hamiltonians")
+    ap.add_argument("--use-qubits", type=int, default=32, help="learned: qubits of the step-choice queries")
     ap.add_argument("--qubits", type=int, default=30,
                     help="state size; values other than 30 are for profiling captures only")
     return ap.parse_args()
@@ -583,6 +585,98 @@ def run_batched(args):
         dist.destroy_process_group()
 
 
+# ---------------------------------------------------------------- learned
+
+def run_learned(args):
+    """Learned step choice: train the network on Trotter errors the batched
+    engine measures (complex128, n 14..18, 200-2000 terms, 8 times, r = 1..64
+    plus the Richardson reference runs), then choose r for error 1e-3 on a
+    1000-term Hamiltonian at n = 32 (complex64, 32 GiB state) and judge the
+    choice with the doubling sweep."""
+    import torch
+    import paper_2504_17881_gb300 as ps
+    from paper_2504_17881_gb300 import learned
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if rank != 0:
+        return
+    eps = 1e-3
+    P = args.train_problems
+    t0 = time.perf_counter()
+    probs = learned.synthetic_problems(P, seed=1000, n_range=(14, 18), L_range=(200, 2000))
+    times = learned.TIMES16[::2]
+    torch.cuda.synchronize()
+    tg = time.perf_counter()
+    X, y, info = learned.training_rows(probs, times=times)
+    torch.cuda.synchronize()
+    gen_s = time.perf_counter() - tg
+    gen_rot = sum(probs[pi].L * r for pi in range(P) for _ in times for r in (1, 2, 4, 8, 16, 32, 64, 128))
+    hold = 16
+    cut = (P - hold) * len(times) * len(learned.R_VALUES)
+    m = learned.StepPredictor(seed=2)
+    tt = time.perf_counter()
+    losses = m.fit(X[:cut], y[:cut], epochs=150, batch=256, lr=2e-3, seed=3)
+    train_s = time.perf_counter() - tt
+    pv = m.predict(X[cut:])
+    val_rms = float(np.sqrt(np.mean((pv - y[cut:]) ** 2)))
+    margin = m.calibrate_margin(X[cut:], y[cut:], 0.8)
+    del X, y, info, probs
+    torch.cuda.empty_cache()
+
+    # use: n = use_qubits, 1000 terms, complex64
+    n = args.use_qubits
+    from paper_2504_17881_gb300 import inputs
+    x, z, h = inputs.jw_hamiltonian(n, 1000, seed=1500)
+    prob = learned.Problem(n, x, z, h, psi_seed=1500)
+    queries = []
+    for t in (0.5, 1.0):
+        tq = time.perf_counter()
+        r_ml, _ = m.pick_r(prob, t, eps)
+        pick_s = time.perf_counter() - tq
+        ts = time.perf_counter()
+        r_sw, rot_sw, g_sw = learned.sweep(prob, t, eps, r_max=256)
+        torch.cuda.synchronize()
+        sweep_s = time.perf_counter() - ts
+        # judge: the learned pick's run against the sweep's last (finest) run, 2 r_sw
+        tl = time.perf_counter()
+        psi0 = ps.StateVector(n, tensor=learned.initial_state(n, prob.psi_seed, torch.complex64, "cuda"))
+        work = ps.StateVector(n, dtype=torch.complex64)
+        work.copy_from(psi0)
+        work.evolve_trotter(prob.ham, t, r_ml)
+        g_ml = work.overlap(psi0)
+        torch.cuda.synchronize()
+        learned_s = time.perf_counter() - tl
+        work.copy_from(psi0)
+        work.evolve_trotter(prob.ham, t, 2 * r_sw)
+        g_fine = work.overlap(psi0)
+        del work, psi0
+        torch.cuda.empty_cache()
+        queries.append({"t": t, "r_sweep": r_sw, "rotations_sweep": rot_sw, "sweep_s": sweep_s,
+                        "r_learned": r_ml, "rotations_learned": r_ml * prob.L, "learned_run_s": learned_s,
+                        "pick_s": pick_s, "r_bound": learned.bound_r(prob, t, eps),
+                        "err_learned_vs_2r_sweep": abs(g_ml - g_fine),
+                        "err_sweep_estimate": 2 * abs(g_sw - g_fine),
+                        "rotation_ratio_sweep_over_learned": rot_sw / max(1, r_ml * prob.L)})
+    tot_sw = sum(q["rotations_sweep"] for q in queries)
+    tot_ml = sum(q["rotations_learned"] for q in queries)
+    line = {
+        "metric": "learned Trotter step choice: rotations spent by the doubling sweep / by the learned pick "
+                  f"(n={n} complex64, eps=1e-3)",
+        "value": tot_sw / max(1, tot_ml), "unit": "x", "n_gpus": 1, "higher_is_better": True, "data": "synthetic",
+        "dtype": "f32 network, c128 training data, c64 use",
+        "config": {"workload": f"train: {P} JW-like H (n 14..18, 200-2000 terms), {len(times)} times 0.1..2.5, "
+                               f"r 1..64; use: n={n}, 1000 terms, 8-determinant state",
+                   "training_rows": int(cut), "held_out_rows": int(len(pv)),
+                   "network": "12 -> 128 -> 128 -> 128 -> 1, tanh, FP32, Adam"},
+        "training": {"data_generation_s": gen_s, "data_rotations": gen_rot, "train_s": train_s,
+                     "loss_first": float(losses[0]), "loss_last": float(losses[-1]), "val_rms_log_eps": val_rms,
+                     "margin": margin, "total_s": time.perf_counter() - t0},
+        "queries": queries, "rotations_sweep": tot_sw, "rotations_learned": tot_ml,
+    }
+    print(json.dumps(line), flush=True)
+
+
 # -------------------------------------------------------------- reference
 
 def run_reference(args):
@@ -633,6 +727,8 @@ def main():
         run_reference(args)
     elif args.workload == "batched":
         run_batched(args)
+    elif args.workload == "learned":
+        run_learned(args)
     else:
         run_ours(args)
 

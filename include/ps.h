@@ -396,10 +396,11 @@ int ps_ham_trotter_bound(const ps_ham *ham, size_t L_D, double *out);
 int ps_ham_error_coefficient(ps_ham *ham, const uint64_t *idx, const double *amp, size_t ndet, double *out);
 
 /* PS_MLP_FEATURES floats describing "first-order Trotter with r steps to
- * time t from psi" (t > 0, r >= 1; psi as for ps_ham_error_coefficient):
- *   n / 32, log L, log lambda, log(max|h| / lambda), log t, log r, log C,
- *   log(C t^2 / r), one-norm fraction of diagonal terms (x = 0),
- *   sum_l |h_l| popc(x_l | z_l) / (lambda n),
+ * time t from psi" (t > 0, r >= 1; psi as for ps_ham_error_coefficient),
+ * none growing with n by itself:
+ *   C / (4 lambda^2), log L, log lambda, log(max|h| / lambda), log t, log r,
+ *   log C, log(C t^2 / r), one-norm fraction of diagonal terms (x = 0),
+ *   log(sum_l |h_l| popc(x_l | z_l) / lambda),
  *   k = log max(|K| / lambda^2, 1e-12),  k + log(lambda^2 t^2 / r),
  * C = ps_ham_trotter_bound(ham, L) (computed once per handle and cached).
  * PS_ERR_ARG when every pair of terms commutes (C = 0). Host only. */
@@ -469,6 +470,11 @@ int ps_mlp_predict(ps_mlp *m, const float *x_dev, size_t rows, float *y_dev);
  * Synchronous. */
 int ps_mlp_pick_r(ps_mlp *m, ps_ham *ham, const uint64_t *idx, const double *amp, size_t ndet, double t, double eps,
                   double margin, uint32_t r_max, uint32_t *r_out, float *pred_out);
+/* The same for an ensemble of `count` (1..64) networks on one device: the
+ * prediction is the mean of the members' predicted log errors. */
+int ps_mlp_pick_r_ensemble(ps_mlp *const *nets, int count, ps_ham *ham, const uint64_t *idx, const double *amp,
+                           size_t ndet, double t, double eps, double margin, uint32_t r_max, uint32_t *r_out,
+                           float *pred_out);
 
 #ifdef __cplusplus
 }

@@ -97,8 +97,8 @@ def error_coefficient(n: int, x, z, h, psi: np.ndarray) -> complex:
 
 def features(n: int, x, z, h, t: float, r: int, psi: np.ndarray) -> np.ndarray:
     """Feature vector of the query "first-order Trotter, r steps, time t,
-    initial state psi":
-      0  n / 32
+    initial state psi" (none grows with n by itself):
+      0  C / (4 lambda^2)                (the one-norm-weighted fraction of anticommuting pairs)
       1  log L
       2  log lambda                      (lambda = sum |h|)
       3  log(max |h| / lambda)
@@ -107,7 +107,7 @@ def features(n: int, x, z, h, t: float, r: int, psi: np.ndarray) -> np.ndarray:
       6  log C                           (C = trotter_bound with L_D = L)
       7  log(C t^2 / r)                  (the bound's error scale)
       8  sum over diagonal terms (x = 0) of |h| / lambda
-      9  sum_l |h_l| |support(P_l)| / (lambda n)
+      9  log(sum_l |h_l| |support(P_l)| / lambda)   (mean support size)
      10  log(max(|K| / lambda^2, K_FLOOR))     (K = error_coefficient)
      11  feature 10 + log(lambda^2 t^2 / r)    (the leading-order error of the overlap)
     """
@@ -119,9 +119,9 @@ def features(n: int, x, z, h, t: float, r: int, psi: np.ndarray) -> np.ndarray:
     for a, xv, zv in zip(hab, x, z):
         supp += a * bin(int(xv) | int(zv)).count("1")
     k = math.log(max(abs(error_coefficient(n, x, z, h, psi)) / (lam * lam), K_FLOOR))
-    return np.array([n / 32.0, math.log(len(h)), math.log(lam), math.log(max(hab) / lam), math.log(t),
+    return np.array([C / (4.0 * lam * lam), math.log(len(h)), math.log(lam), math.log(max(hab) / lam), math.log(t),
                      math.log(r), math.log(C), math.log(C) + 2.0 * math.log(t) - math.log(r), diag / lam,
-                     supp / (lam * n), k, k + 2.0 * math.log(lam * t) - math.log(r)], dtype=np.float64)
+                     math.log(supp / lam), k, k + 2.0 * math.log(lam * t) - math.log(r)], dtype=np.float64)
 
 
 # ------------------------------------------------------------------- MLP

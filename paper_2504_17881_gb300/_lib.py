@@ -140,6 +140,7 @@ _SIGS = {
     "ps_mlp_train": (_i, [_vp, _vp, _vp, _sz, ctypes.POINTER(ps_mlp_train_config), _vp]),
     "ps_mlp_predict": (_i, [_vp, _vp, _sz, _vp]),
     "ps_mlp_pick_r": (_i, [_vp, _vp, _vp, _vp, _sz, _d, _d, _d, _u32, ctypes.POINTER(_u32), _vp]),
+    "ps_mlp_pick_r_ensemble": (_i, [_vp, _i, _vp, _vp, _vp, _sz, _d, _d, _d, _u32, ctypes.POINTER(_u32), _vp]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _fn = getattr(lib, _name)
@@ -585,6 +586,19 @@ def ps_mlp_pick_r(m: int, ham: int, idx, amp, t: float, eps: float, margin: floa
     pred = np.zeros(r_max, dtype=np.float32)
     rc = lib.ps_mlp_pick_r(ctypes.c_void_p(m), ctypes.c_void_p(ham), _ptr(i), _ptr(a), len(i), t, eps, margin, r_max,
                            ctypes.byref(r), _ptr(pred))
+    if rc not in (PS_OK, PS_ERR_UNSUPPORTED):
+        _check(rc)
+    return int(r.value), pred
+
+
+def ps_mlp_pick_r_ensemble(nets, ham: int, idx, amp, t: float, eps: float, margin: float, r_max: int):
+    """Returns (r, mean predictions for r = 1..r_max); r = 0 when none qualifies."""
+    i, a = _sparse(idx, amp)
+    arr = (ctypes.c_void_p * len(nets))(*nets)
+    r = _u32()
+    pred = np.zeros(r_max, dtype=np.float32)
+    rc = lib.ps_mlp_pick_r_ensemble(arr, len(nets), ctypes.c_void_p(ham), _ptr(i), _ptr(a), len(i), t, eps, margin,
+                                    r_max, ctypes.byref(r), _ptr(pred))
     if rc not in (PS_OK, PS_ERR_UNSUPPORTED):
         _check(rc)
     return int(r.value), pred

@@ -128,9 +128,10 @@ bool same_state(const SparseState &a, const SparseState &b) {
 }  // namespace
 
 // Features of "first-order Trotter with r steps to time t from psi"
-// (PS_MLP_FEATURES): n / 32, log L, log lambda, log(max|h| / lambda), log t,
-// log r, log C, log(C t^2 / r), diagonal weight fraction, mean support
-// fraction, log max(|K| / lambda^2, 1e-12), and that plus log(lambda^2 t^2 / r);
+// (PS_MLP_FEATURES), none of which grows with n by itself:
+// C / (4 lambda^2), log L, log lambda, log(max|h| / lambda), log t, log r,
+// log C, log(C t^2 / r), diagonal weight fraction, log mean support size,
+// log max(|K| / lambda^2, 1e-12), and that plus log(lambda^2 t^2 / r);
 // C the bound above for L_D = L, K the error coefficient on psi.
 void query_features(const Ham &H, double C, double K_abs, double t, uint32_t r, float *out) {
     double lam = 0.0, hmax = 0.0, diag = 0.0, supp = 0.0;
@@ -142,7 +143,7 @@ void query_features(const Ham &H, double C, double K_abs, double t, uint32_t r, 
         supp += a * (double)__builtin_popcountll(H.x[l] | H.z[l]);
     }
     const double logC = std::log(C);
-    out[0] = (float)(H.n / 32.0);
+    out[0] = (float)(C / (4.0 * lam * lam));
     out[1] = (float)std::log((double)H.h.size());
     out[2] = (float)std::log(lam);
     out[3] = (float)std::log(hmax / lam);
@@ -151,7 +152,7 @@ void query_features(const Ham &H, double C, double K_abs, double t, uint32_t r, 
     out[6] = (float)logC;
     out[7] = (float)(logC + 2.0 * std::log(t) - std::log((double)r));
     out[8] = (float)(diag / lam);
-    out[9] = (float)(supp / (lam * H.n));
+    out[9] = (float)std::log(supp / lam);
     const double k = std::log(std::max(K_abs / (lam * lam), 1e-12));
     out[10] = (float)k;
     out[11] = (float)(k + 2.0 * std::log(lam * t) - std::log((double)r));

@@ -388,34 +388,46 @@ int ps_mlp_predict(ps_mlp *m, const float *x_dev, size_t rows, float *y_dev) {
     return e ? cuda_mfail((cudaError_t)e, "MLP inference kernels") : PS_OK;
 }
 
-int ps_mlp_pick_r(ps_mlp *m, ps_ham *ham, const uint64_t *idx, const double *amp, size_t ndet, double t, double eps,
-                  double margin, uint32_t r_max, uint32_t *r_out, float *pred_out) {
-    if (!m || !ham || !r_out) return mfail(PS_ERR_ARG, "null argument");
-    if (m->n_in != kMlpFeatures) return mfail(PS_ERR_ARG, "the network must take the query features");
+int ps_mlp_pick_r_ensemble(ps_mlp *const *nets, int count, ps_ham *ham, const uint64_t *idx, const double *amp,
+                           size_t ndet, double t, double eps, double margin, uint32_t r_max, uint32_t *r_out,
+                           float *pred_out) {
+    if (!nets || count < 1 || count > 64 || !ham || !r_out) return mfail(PS_ERR_ARG, "null argument or bad count");
+    for (int k = 0; k < count; ++k) {
+        if (!nets[k]) return mfail(PS_ERR_ARG, "null network");
+        if (nets[k]->n_in != kMlpFeatures) return mfail(PS_ERR_ARG, "the network must take the query features");
+        if (nets[k]->device != nets[0]->device) return mfail(PS_ERR_ARG, "networks on different devices");
+    }
     if (!(eps > 0.0)) return mfail(PS_ERR_ARG, "eps must be positive");
     if (r_max < 1 || r_max > (1u << 20)) return mfail(PS_ERR_ARG, "r_max must be in [1, 2^20]");
     *r_out = 0;
     std::vector<float> f((size_t)r_max * kMlpFeatures);
     for (uint32_t r = 1; r <= r_max; ++r)
         if (int rc = ham_query_features(ham, idx, amp, ndet, t, r, &f[(size_t)(r - 1) * kMlpFeatures])) return rc;
-    Guard g(m->device);
+    ps_mlp *m0 = nets[0];
+    Guard g(m0->device);
     float *d = nullptr;
-    cudaError_t ce = cudaMalloc((void **)&d, sizeof(float) * ((size_t)r_max * kMlpFeatures + r_max));
+    cudaError_t ce = cudaMalloc((void **)&d, sizeof(float) * ((size_t)r_max * kMlpFeatures + (size_t)count * r_max));
     if (ce != cudaSuccess) return cuda_mfail(ce, "pick_r buffers");
     float *dy = d + (size_t)r_max * kMlpFeatures;
-    std::vector<float> pred(r_max);
+    std::vector<float> all((size_t)count * r_max), pred(r_max, 0.f);
     int rc = PS_OK;
-    ce = cudaMemcpyAsync(d, f.data(), sizeof(float) * f.size(), cudaMemcpyHostToDevice, m->stream);
-    if (ce == cudaSuccess) {
-        rc = ps_mlp_predict(m, d, r_max, dy);
-        if (rc == PS_OK) {
-            ce = cudaMemcpyAsync(pred.data(), dy, sizeof(float) * r_max, cudaMemcpyDeviceToHost, m->stream);
-            if (ce == cudaSuccess) ce = cudaStreamSynchronize(m->stream);
-        }
+    ce = cudaMemcpyAsync(d, f.data(), sizeof(float) * f.size(), cudaMemcpyHostToDevice, m0->stream);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(m0->stream);
+    for (int k = 0; k < count && rc == PS_OK && ce == cudaSuccess; ++k) {
+        rc = ps_mlp_predict(nets[k], d, r_max, dy + (size_t)k * r_max);
+        if (rc == PS_OK) ce = cudaStreamSynchronize(nets[k]->stream);
     }
+    if (rc == PS_OK && ce == cudaSuccess)
+        ce = cudaMemcpy(all.data(), dy, sizeof(float) * all.size(), cudaMemcpyDeviceToHost);
     cudaFree(d);
     if (rc) return rc;
     if (ce != cudaSuccess) return cuda_mfail(ce, "pick_r transfer");
+    // the ensemble's prediction: the mean of the members' log errors, in member order
+    for (uint32_t r = 0; r < r_max; ++r) {
+        double s = 0.0;
+        for (int k = 0; k < count; ++k) s += all[(size_t)k * r_max + r];
+        pred[r] = (float)(s / count);
+    }
     if (pred_out) std::memcpy(pred_out, pred.data(), sizeof(float) * r_max);
     const double target = std::log(eps) - margin;
     for (uint32_t r = 1; r <= r_max; ++r)
@@ -426,6 +438,11 @@ int ps_mlp_pick_r(ps_mlp *m, ps_ham *ham, const uint64_t *idx, const double *amp
     std::ostringstream os;
     os << "no r <= " << r_max << " has a predicted log error below " << target;
     return mfail(PS_ERR_UNSUPPORTED, os.str());
+}
+
+int ps_mlp_pick_r(ps_mlp *m, ps_ham *ham, const uint64_t *idx, const double *amp, size_t ndet, double t, double eps,
+                  double margin, uint32_t r_max, uint32_t *r_out, float *pred_out) {
+    return ps_mlp_pick_r_ensemble(&m, 1, ham, idx, amp, ndet, t, eps, margin, r_max, r_out, pred_out);
 }
 
 }  // extern "C"

@@ -221,6 +221,37 @@ class StepPredictor:
         self.margin = float(d["margin"])
 
 
+class StepEnsemble:
+    """Several independently seeded predictors trained on the same rows; the
+    prediction is the mean of their predicted log errors (lower variance than
+    any one network)."""
+
+    def __init__(self, count: int = 4, seed: int = 0, stream=None):
+        self.members = [StepPredictor(seed=seed + 101 * k, stream=stream) for k in range(count)]
+        self.margin = 0.0
+
+    def fit(self, X, y, epochs=150, batch=256, lr=2e-3, seed=0):
+        return [mb.fit(X, y, epochs=epochs, batch=batch, lr=lr, seed=seed + 7 * k)
+                for k, mb in enumerate(self.members)]
+
+    def predict(self, X) -> np.ndarray:
+        return np.mean([mb.predict(X) for mb in self.members], axis=0)
+
+    def calibrate_margin(self, X_val, y_val, quantile: float = 0.8) -> float:
+        resid = np.asarray(y_val, np.float64) - self.predict(X_val)
+        self.margin = max(0.0, float(np.quantile(resid, quantile)))
+        return self.margin
+
+    def pick_r(self, problem: Problem, t: float, eps: float = 1e-3, margin: float | None = None, r_max: int = 4096):
+        m = self.margin if margin is None else margin
+        return _lib.ps_mlp_pick_r_ensemble([mb.handle for mb in self.members], problem.ham.handle, problem.det_idx,
+                                           problem.det_amp, t, eps, m, r_max)
+
+    def close(self):
+        for mb in self.members:
+            mb.close()
+
+
 def sweep(problem: Problem, t: float, eps: float = 1e-3, r_max: int = 4096, dtype=None):
     """The plain doubling sweep on one GPU state: (r, rotations applied, g_r)."""
     import torch
@@ -262,5 +293,5 @@ def reference_overlap(problem: Problem, t: float, R: int = 256, dtype=None) -> c
     return richardson3(g[(0, 0, R)], g[(0, 0, 2 * R)], g[(0, 0, 4 * R)])
 
 
-__all__ = ["StepPredictor", "Problem", "synthetic_problems", "training_rows", "overlaps_by_batch", "sweep",
+__all__ = ["StepPredictor", "StepEnsemble", "Problem", "synthetic_problems", "training_rows", "overlaps_by_batch", "sweep",
            "bound_r", "run_error", "reference_overlap", "richardson3", "TIMES16", "R_VALUES"]

@@ -151,19 +151,21 @@ def test_features_and_bound_match_oracle():
             assert H.trotter_bound(L_D) == pytest.approx(OL.trotter_bound(n, x, z, h, L_D), rel=1e-12)
 
 
-NPROB = 160
+NPROB = 480
+NHOLD = 48
 
 
 @pytest.fixture(scope="module")
 def trained():
-    """A predictor trained on batched-engine errors of small problems; the
-    last 24 problems are held out to calibrate the pick margin."""
+    """An ensemble of four predictors trained on batched-engine errors of
+    small problems; the last NHOLD problems are held out to calibrate the
+    pick margin."""
     probs = learned.synthetic_problems(NPROB, seed=1000, n_range=(8, 12), L_range=(40, 160), lam_range=(1.5, 5.0))
     times = learned.TIMES16[::2]
     X, y, info = learned.training_rows(probs, times=times)
-    cut = (NPROB - 24) * len(times) * len(learned.R_VALUES)
-    m = learned.StepPredictor(seed=2)
-    losses = m.fit(X[:cut], y[:cut], epochs=150, batch=256, lr=2e-3, seed=3)
+    cut = (NPROB - NHOLD) * len(times) * len(learned.R_VALUES)
+    m = learned.StepEnsemble(count=4, seed=2)
+    losses = m.fit(X[:cut], y[:cut], epochs=150, batch=256, lr=2e-3, seed=3)[0]
     m.calibrate_margin(X[cut:], y[cut:], 0.8)
     return m, X, y, losses
 

@@ -73,8 +73,8 @@ def test_features_hand_example():
     C = 4 * (0.5 * 0.25 + 0.25 * (0.5 + 0.25) + 0.25 * 0.25)
     # K on |00>: pair (X1, Z1Z2): h2 h1 <00|Z1Z2 X1|00> = 0 (X1 flips qubit 1);
     # pair (Z1Z2, Y2): h3 h2 <00|Y2 Z1Z2|00> = 0 (Y2 flips qubit 2)
-    expect = [2 / 32, math.log(3), math.log(lam), math.log(0.5), math.log(t), math.log(r), math.log(C),
-              math.log(C * t * t / r), 0.25, (0.5 * 1 + 0.25 * 2 + 0.25 * 1) / (lam * 2), math.log(L.K_FLOOR),
+    expect = [C / 4, math.log(3), math.log(lam), math.log(0.5), math.log(t), math.log(r), math.log(C),
+              math.log(C * t * t / r), 0.25, math.log(0.5 * 1 + 0.25 * 2 + 0.25 * 1), math.log(L.K_FLOOR),
               math.log(L.K_FLOOR) + 2 * math.log(t) - math.log(r)]
     assert np.allclose(f, expect, rtol=1e-14, atol=1e-15)
 
