@@ -72,7 +72,7 @@ def parse():
     ap.add_argument("--batch-runs", type=int, default=BATCH_RUNS)
     ap.add_argument("--no-sequential", action="store_true", help="batched: skip the one-run-at-a-time comparison")
     ap.add_argument("--no-autotune", action="store_true", help="batched: default lane size and tile bits")
-    ap.add_argument("--train-problems", type=int, default=96, help="learned: training Hamiltonians")
+    ap.add_argument("--train-problems", type=int, default=128, help="learned: training Hamiltonians")
     ap.add_argument("--use-qubits", type=int, default=32, help="learned: qubits of the step-choice queries")
     ap.add_argument("--qubits", type=int, default=30,
                     help="state size; values other than 30 are for profiling captures only")
@@ -604,7 +604,8 @@ def run_learned(args):
     eps = 1e-3
     P = args.train_problems
     t0 = time.perf_counter()
-    probs = learned.synthetic_problems(P, seed=1000, n_range=(14, 18), L_range=(200, 2000))
+    probs = learned.synthetic_problems(P, seed=1000, n_range=(14, 18), L_range=(200, 2000), lam_range=(1.0, 10.0),
+                                       far_every=2)
     times = learned.TIMES16[::2]
     torch.cuda.synchronize()
     tg = time.perf_counter()
@@ -614,9 +615,9 @@ def run_learned(args):
     gen_rot = sum(probs[pi].L * r for pi in range(P) for _ in times for r in (1, 2, 4, 8, 16, 32, 64, 128))
     hold = 16
     cut = (P - hold) * len(times) * len(learned.R_VALUES)
-    m = learned.StepPredictor(seed=2)
+    m = learned.StepEnsemble(count=4, seed=2)
     tt = time.perf_counter()
-    losses = m.fit(X[:cut], y[:cut], epochs=150, batch=256, lr=2e-3, seed=3)
+    losses = m.fit(X[:cut], y[:cut], epochs=150, batch=256, lr=2e-3, seed=3)[0]
     train_s = time.perf_counter() - tt
     pv = m.predict(X[cut:])
     val_rms = float(np.sqrt(np.mean((pv - y[cut:]) ** 2)))
@@ -627,10 +628,10 @@ def run_learned(args):
     # use: n = use_qubits, 1000 terms, complex64
     n = args.use_qubits
     from paper_2504_17881_gb300 import inputs
-    x, z, h = inputs.jw_hamiltonian(n, 1000, seed=1500)
+    x, z, h = inputs.jw_hamiltonian(n, 1000, seed=1500, lam=8.0)
     prob = learned.Problem(n, x, z, h, psi_seed=1500)
     queries = []
-    for t in (0.5, 1.0):
+    for t in (1.0, 2.0):
         tq = time.perf_counter()
         r_ml, _ = m.pick_r(prob, t, eps)
         pick_s = time.perf_counter() - tq
@@ -640,7 +641,7 @@ def run_learned(args):
         sweep_s = time.perf_counter() - ts
         # judge: the learned pick's run against the sweep's last (finest) run, 2 r_sw
         tl = time.perf_counter()
-        psi0 = ps.StateVector(n, tensor=learned.initial_state(n, prob.psi_seed, torch.complex64, "cuda"))
+        psi0 = ps.StateVector(n, tensor=prob.state(torch.complex64))
         work = ps.StateVector(n, dtype=torch.complex64)
         work.copy_from(psi0)
         work.evolve_trotter(prob.ham, t, r_ml)
@@ -665,10 +666,10 @@ def run_learned(args):
                   f"(n={n} complex64, eps=1e-3)",
         "value": tot_sw / max(1, tot_ml), "unit": "x", "n_gpus": 1, "higher_is_better": True, "data": "synthetic",
         "dtype": "f32 network, c128 training data, c64 use",
-        "config": {"workload": f"train: {P} JW-like H (n 14..18, 200-2000 terms), {len(times)} times 0.1..2.5, "
-                               f"r 1..64; use: n={n}, 1000 terms, 8-determinant state",
+        "config": {"workload": f"train: {P} JW-like H (n 14..18, 200-2000 terms, one-norm 1..10; every 2nd guiding state "
+                               f"with determinants >= 10 flips apart), {len(times)} times 0.1..2.5, r 1..64; use: n={n}, 1000 terms, one-norm 8, 8-determinant state",
                    "training_rows": int(cut), "held_out_rows": int(len(pv)),
-                   "network": "12 -> 128 -> 128 -> 128 -> 1, tanh, FP32, Adam"},
+                   "network": "4 x (12 -> 128 -> 128 -> 128 -> 1, tanh, FP32, Adam), mean of log errors"},
         "training": {"data_generation_s": gen_s, "data_rotations": gen_rot, "train_s": train_s,
                      "loss_first": float(losses[0]), "loss_last": float(losses[-1]), "val_rms_log_eps": val_rms,
                      "margin": margin, "total_s": time.perf_counter() - t0},

@@ -390,18 +390,20 @@ int ps_ham_trotter_bound(const ps_ham *ham, size_t L_D, double *out);
  *   K = sum_{k < l, P_k P_l = -P_l P_k} h_l h_k <psi|P_l P_k|psi>,
  * term k applied before term l.  One Trotter step of size delta equals
  * exp(i delta H - (delta^2 / 2) sum_{l>k} h_l h_k [P_l, P_k] + O(delta^3)),
- * so g_r(t) - g(t) = -(t^2 / r) K + O(t^3 / r).  out = (re, im).  Cached per
- * handle for the last state.  Host only, O(L^2) with a cheap rejection of
- * pairs whose X masks differ by no difference of two basis states of psi. */
+ * so g_r(t) - g(t) = -(t^2 / r) K + O(t^3 / r).  out = (re of K, im of K,
+ * ||E2 psi||^2) with E2 = -sum_{k < l anticommuting} h_l h_k P_l P_k the
+ * second-order exponent: when K vanishes the error starts at
+ * -(t^4 / (2 r^2)) ||E2 psi||^2.  Cached per handle for the last state.
+ * Host only, O(L^2 ndet) (host threads for E2). */
 int ps_ham_error_coefficient(ps_ham *ham, const uint64_t *idx, const double *amp, size_t ndet, double *out);
 
 /* PS_MLP_FEATURES floats describing "first-order Trotter with r steps to
- * time t from psi" (t > 0, r >= 1; psi as for ps_ham_error_coefficient),
- * none growing with n by itself:
- *   C / (4 lambda^2), log L, log lambda, log(max|h| / lambda), log t, log r,
- *   log C, log(C t^2 / r), one-norm fraction of diagonal terms (x = 0),
- *   log(sum_l |h_l| popc(x_l | z_l) / lambda),
- *   k = log max(|K| / lambda^2, 1e-12),  k + log(lambda^2 t^2 / r),
+ * time t from psi" (t > 0, r >= 1; psi as for ps_ham_error_coefficient):
+ *   log L, log lambda, log(max|h| / lambda), log t, log r, log C,
+ *   log(C t^2 / r), one-norm fraction of diagonal terms (x = 0),
+ *   log max(|K| / lambda^2, 1e-6),  log max(||E2 psi||^2 / lambda^4, 1e-6),
+ *   log(e1 + e2) and e1 / (e1 + e2) for the error estimates e1 = |K| t^2 / r
+ *   and e2 = ||E2 psi||^2 t^4 / (2 r^2) (the sum floored at 1e-6 lambda^2 t^2 / r),
  * C = ps_ham_trotter_bound(ham, L) (computed once per handle and cached).
  * PS_ERR_ARG when every pair of terms commutes (C = 0). Host only. */
 int ps_ham_features(ps_ham *ham, const uint64_t *idx, const double *amp, size_t ndet, double t, uint32_t r,

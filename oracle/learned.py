@@ -25,7 +25,7 @@ import math
 import numpy as np
 
 N_FEATURES = 12
-K_FLOOR = 1e-12
+K_FLOOR = 1e-6
 
 
 # ------------------------------------------------------------ Pauli algebra
@@ -95,33 +95,52 @@ def error_coefficient(n: int, x, z, h, psi: np.ndarray) -> complex:
     return complex(K)
 
 
+def second_order_norm2(n: int, x, z, h, psi: np.ndarray) -> float:
+    """||E2 psi||^2 with E2 = -(1/2) sum_{l>k} h_l h_k [P_l, P_k] = -sum over
+    anticommuting pairs k < l of h_l h_k P_l P_k, the second-order term of one
+    Trotter step's exponent.  When K = 0 the overlap error starts at
+    (t^4 / (2 r^2)) <psi|E2^2|psi> = -(t^4 / (2 r^2)) ||E2 psi||^2."""
+    L = len(h)
+    v = np.zeros_like(psi)
+    for k in range(L):
+        pk = pauli_apply(n, int(x[k]), int(z[k]), psi)
+        for l in range(k + 1, L):
+            if anticommute(n, int(x[l]), int(z[l]), int(x[k]), int(z[k])):
+                v += float(h[l]) * float(h[k]) * pauli_apply(n, int(x[l]), int(z[l]), pk)
+    return float(np.vdot(v, v).real)
+
+
 def features(n: int, x, z, h, t: float, r: int, psi: np.ndarray) -> np.ndarray:
     """Feature vector of the query "first-order Trotter, r steps, time t,
-    initial state psi" (none grows with n by itself):
-      0  C / (4 lambda^2)                (the one-norm-weighted fraction of anticommuting pairs)
-      1  log L
-      2  log lambda                      (lambda = sum |h|)
-      3  log(max |h| / lambda)
-      4  log t
-      5  log r
-      6  log C                           (C = trotter_bound with L_D = L)
-      7  log(C t^2 / r)                  (the bound's error scale)
-      8  sum over diagonal terms (x = 0) of |h| / lambda
-      9  log(sum_l |h_l| |support(P_l)| / lambda)   (mean support size)
-     10  log(max(|K| / lambda^2, K_FLOOR))     (K = error_coefficient)
-     11  feature 10 + log(lambda^2 t^2 / r)    (the leading-order error of the overlap)
+    initial state psi":
+      0  log L
+      1  log lambda                      (lambda = sum |h|)
+      2  log(max |h| / lambda)
+      3  log t
+      4  log r
+      5  log C                           (C = trotter_bound with L_D = L)
+      6  log(C t^2 / r)                  (the bound's error scale)
+      7  sum over diagonal terms (x = 0) of |h| / lambda
+      8  log(max(|K| / lambda^2, K_FLOOR))             (K = error_coefficient)
+      9  log(max(||E2 psi||^2 / lambda^4, K_FLOOR))    (second_order_norm2)
+     10  log(e1 + e2), e1 = |K| t^2 / r, e2 = ||E2 psi||^2 t^4 / (2 r^2)
+                                        (the first- and second-order estimates of the overlap error)
+     11  e1 / (e1 + e2)                 (the first-order share; 0 when both vanish)
     """
     hab = [abs(float(v)) for v in h]
     lam = sum(hab)
     C = trotter_bound(n, x, z, h)
     diag = sum(a for a, xv in zip(hab, x) if int(xv) == 0)
-    supp = 0.0
-    for a, xv, zv in zip(hab, x, z):
-        supp += a * bin(int(xv) | int(zv)).count("1")
-    k = math.log(max(abs(error_coefficient(n, x, z, h, psi)) / (lam * lam), K_FLOOR))
-    return np.array([C / (4.0 * lam * lam), math.log(len(h)), math.log(lam), math.log(max(hab) / lam), math.log(t),
-                     math.log(r), math.log(C), math.log(C) + 2.0 * math.log(t) - math.log(r), diag / lam,
-                     math.log(supp / lam), k, k + 2.0 * math.log(lam * t) - math.log(r)], dtype=np.float64)
+    K = abs(error_coefficient(n, x, z, h, psi))
+    N2 = second_order_norm2(n, x, z, h, psi)
+    e1 = K * t * t / r
+    e2 = N2 * t ** 4 / (2.0 * r * r)
+    est = math.log(max(e1 + e2, K_FLOOR * lam * lam * t * t / r))
+    share = e1 / (e1 + e2) if e1 + e2 > 0 else 0.0
+    return np.array([math.log(len(h)), math.log(lam), math.log(max(hab) / lam), math.log(t), math.log(r),
+                     math.log(C), math.log(C) + 2.0 * math.log(t) - math.log(r), diag / lam,
+                     math.log(max(K / (lam * lam), K_FLOOR)), math.log(max(N2 / lam ** 4, K_FLOOR)), est, share],
+                    dtype=np.float64)
 
 
 # ------------------------------------------------------------------- MLP

@@ -141,7 +141,8 @@ class Hamiltonian:
         """Query features for first-order Trotter from the sparse state sum amp_i |idx_i>."""
         return ps_ham_features(self.handle, idx, amp, t, r)
 
-    def error_coefficient(self, idx, amp) -> complex:
+    def error_coefficient(self, idx, amp):
+        """(K, ||E2 psi||^2) of first-order Trotter for the sparse initial state."""
         return ps_ham_error_coefficient(self.handle, idx, amp)
 
     def qdrift_stream(self, t: float, N: int, seed: int, first: int = 0, count: int | None = None):

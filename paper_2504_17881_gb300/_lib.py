@@ -474,11 +474,12 @@ def ps_ham_features(ham: int, idx, amp, t: float, r: int) -> np.ndarray:
     return out
 
 
-def ps_ham_error_coefficient(ham: int, idx, amp) -> complex:
+def ps_ham_error_coefficient(ham: int, idx, amp):
+    """(K, ||E2 psi||^2) for the sparse state sum amp_i |idx_i>."""
     i, a = _sparse(idx, amp)
-    out = np.zeros(2, dtype=np.float64)
+    out = np.zeros(3, dtype=np.float64)
     _check(lib.ps_ham_error_coefficient(ctypes.c_void_p(ham), _ptr(i), _ptr(a), len(i), _ptr(out)))
-    return complex(out[0], out[1])
+    return complex(out[0], out[1]), float(out[2])
 
 
 def ps_trotter_stream(ham: int, L: int, t: float, r: int):

@@ -223,9 +223,10 @@ struct SparseState {
 };
 
 // Features of "first-order Trotter, r steps to time t from psi" for a
-// Hamiltonian whose bound (every term deterministic) is C and whose
-// leading-order error coefficient on psi has modulus K_abs.
-void query_features(const Ham &H, double C, double K_abs, double t, uint32_t r, float *out);
+// Hamiltonian whose bound (every term deterministic) is C, whose
+// leading-order error coefficient on psi has modulus K_abs and whose
+// second-order exponent E2 gives ||E2 psi||^2 = E2_norm2.
+void query_features(const Ham &H, double C, double K_abs, double E2_norm2, double t, uint32_t r, float *out);
 // The same for a Hamiltonian handle (bound and coefficient cached per state).
 int ham_query_features(ps_ham *ham, const uint64_t *idx, const double *amp, size_t ndet, double t, uint32_t r,
                        float *out);
@@ -252,6 +253,6 @@ struct ps_ham {
     double bound_full = -1.0;
     // the error coefficient of the last state it was computed for
     ps::SparseState k_state;
-    double k_re = 0.0, k_im = 0.0;
+    double k_re = 0.0, k_im = 0.0, e2_norm2 = 0.0;
     bool k_valid = false;
 };

@@ -7,6 +7,7 @@
 #include <algorithm>
 #include <cmath>
 #include <sstream>
+#include <thread>
 #include <unordered_map>
 #include <unordered_set>
 #include <vector>
@@ -104,6 +105,60 @@ void error_coefficient(const Ham &H, const SparseState &st, double &Kr, double &
     }
 }
 
+// ||E2 psi||^2 with E2 = -(1/2) sum_{l>k} h_l h_k [P_l, P_k] = -sum over
+// anticommuting pairs k < l of h_l h_k P_l P_k: the second-order term of one
+// Trotter step's exponent.  When K vanishes the overlap error starts at
+// (t^4 / (2 r^2)) <psi|E2^2|psi> = -(t^4 / (2 r^2)) ||E2 psi||^2.  The sparse
+// vector E2 psi is accumulated per thread over slices of k and summed.
+double second_order_norm2(const Ham &H, const SparseState &st) {
+    const size_t L = H.h.size();
+    unsigned nth = std::max(1u, std::min(std::thread::hardware_concurrency(), 32u));
+    nth = (unsigned)std::min<size_t>(nth, std::max<size_t>(1, L / 64));
+    using Map = std::unordered_map<uint64_t, std::pair<double, double>>;
+    std::vector<Map> part(nth);
+    auto work = [&](unsigned tid) {
+        Map &v = part[tid];
+        for (size_t k = tid; k < L; k += nth) {
+            for (size_t l = k + 1; l < L; ++l) {
+                if (!anticommute(H.x[l], H.z[l], H.x[k], H.z[k])) continue;
+                const double w = H.h[l] * H.h[k];
+                for (size_t i = 0; i < st.idx.size(); ++i) {
+                    const uint64_t b = st.idx[i];
+                    double c1r, c1i, c2r, c2i;
+                    pauli_coef(H.x[k], H.z[k], b, c1r, c1i);
+                    pauli_coef(H.x[l], H.z[l], b ^ H.x[k], c2r, c2i);
+                    const double cr = c2r * c1r - c2i * c1i, ci = c2r * c1i + c2i * c1r;
+                    auto &e = v[b ^ H.x[k] ^ H.x[l]];
+                    e.first += w * (cr * st.re[i] - ci * st.im[i]);
+                    e.second += w * (cr * st.im[i] + ci * st.re[i]);
+                }
+            }
+        }
+    };
+    std::vector<std::thread> pool;
+    for (unsigned t = 1; t < nth; ++t) pool.emplace_back(work, t);
+    work(0);
+    for (auto &th : pool) th.join();
+    // merge in thread order, then sum |v|^2 over the sorted keys (a fixed order)
+    Map &all = part[0];
+    for (unsigned t = 1; t < nth; ++t)
+        for (const auto &kv : part[t]) {
+            auto &e = all[kv.first];
+            e.first += kv.second.first;
+            e.second += kv.second.second;
+        }
+    std::vector<uint64_t> keys;
+    keys.reserve(all.size());
+    for (const auto &kv : all) keys.push_back(kv.first);
+    std::sort(keys.begin(), keys.end());
+    double s = 0.0;
+    for (uint64_t key : keys) {
+        const auto &e = all[key];
+        s += e.first * e.first + e.second * e.second;
+    }
+    return s;
+}
+
 int read_state(const Ham &H, const uint64_t *idx, const double *amp, size_t ndet, SparseState &st) {
     if (ndet == 0 || !idx || !amp) return lfail(PS_ERR_ARG, "the initial state needs at least one basis state");
     if (ndet > 65536) return lfail(PS_ERR_ARG, "at most 65536 basis states in a sparse initial state");
@@ -128,34 +183,38 @@ bool same_state(const SparseState &a, const SparseState &b) {
 }  // namespace
 
 // Features of "first-order Trotter with r steps to time t from psi"
-// (PS_MLP_FEATURES), none of which grows with n by itself:
-// C / (4 lambda^2), log L, log lambda, log(max|h| / lambda), log t, log r,
-// log C, log(C t^2 / r), diagonal weight fraction, log mean support size,
-// log max(|K| / lambda^2, 1e-12), and that plus log(lambda^2 t^2 / r);
-// C the bound above for L_D = L, K the error coefficient on psi.
-void query_features(const Ham &H, double C, double K_abs, double t, uint32_t r, float *out) {
-    double lam = 0.0, hmax = 0.0, diag = 0.0, supp = 0.0;
+// (PS_MLP_FEATURES): log L, log lambda, log(max|h| / lambda), log t, log r,
+// log C, log(C t^2 / r), diagonal weight fraction,
+// log max(|K| / lambda^2, 1e-6), log max(||E2 psi||^2 / lambda^4, 1e-6),
+// log(e1 + e2) with the first- and second-order error estimates
+// e1 = |K| t^2 / r and e2 = ||E2 psi||^2 t^4 / (2 r^2) (floored at
+// 1e-6 lambda^2 t^2 / r), and e1 / (e1 + e2); C the bound above for L_D = L,
+// K the error coefficient on psi.
+void query_features(const Ham &H, double C, double K_abs, double E2_norm2, double t, uint32_t r, float *out) {
+    double lam = 0.0, hmax = 0.0, diag = 0.0;
     for (size_t l = 0; l < H.h.size(); ++l) {
         const double a = std::fabs(H.h[l]);
         lam += a;
         hmax = std::max(hmax, a);
         if (H.x[l] == 0) diag += a;
-        supp += a * (double)__builtin_popcountll(H.x[l] | H.z[l]);
     }
     const double logC = std::log(C);
-    out[0] = (float)(C / (4.0 * lam * lam));
-    out[1] = (float)std::log((double)H.h.size());
-    out[2] = (float)std::log(lam);
-    out[3] = (float)std::log(hmax / lam);
-    out[4] = (float)std::log(t);
-    out[5] = (float)std::log((double)r);
-    out[6] = (float)logC;
-    out[7] = (float)(logC + 2.0 * std::log(t) - std::log((double)r));
-    out[8] = (float)(diag / lam);
-    out[9] = (float)std::log(supp / lam);
-    const double k = std::log(std::max(K_abs / (lam * lam), 1e-12));
-    out[10] = (float)k;
-    out[11] = (float)(k + 2.0 * std::log(lam * t) - std::log((double)r));
+    constexpr double kFloor = 1e-6;
+    const double rr = (double)r;
+    const double e1 = K_abs * t * t / rr;
+    const double e2 = E2_norm2 * t * t * t * t / (2.0 * rr * rr);
+    out[0] = (float)std::log((double)H.h.size());
+    out[1] = (float)std::log(lam);
+    out[2] = (float)std::log(hmax / lam);
+    out[3] = (float)std::log(t);
+    out[4] = (float)std::log(rr);
+    out[5] = (float)logC;
+    out[6] = (float)(logC + 2.0 * std::log(t) - std::log(rr));
+    out[7] = (float)(diag / lam);
+    out[8] = (float)std::log(std::max(K_abs / (lam * lam), kFloor));
+    out[9] = (float)std::log(std::max(E2_norm2 / (lam * lam * lam * lam), kFloor));
+    out[10] = (float)std::log(std::max(e1 + e2, kFloor * lam * lam * t * t / rr));
+    out[11] = (float)(e1 + e2 > 0.0 ? e1 / (e1 + e2) : 0.0);
 }
 
 static int ham_coefficient(ps_ham *ham, const uint64_t *idx, const double *amp, size_t ndet) {
@@ -163,6 +222,7 @@ static int ham_coefficient(ps_ham *ham, const uint64_t *idx, const double *amp, 
     if (int rc = read_state(ham->H, idx, amp, ndet, st)) return rc;
     if (!ham->k_valid || !same_state(st, ham->k_state)) {
         error_coefficient(ham->H, st, ham->k_re, ham->k_im);
+        ham->e2_norm2 = second_order_norm2(ham->H, st);
         ham->k_state = std::move(st);
         ham->k_valid = true;
     }
@@ -181,7 +241,7 @@ int ham_query_features(ps_ham *ham, const uint64_t *idx, const double *amp, size
     if (!(lam > 0.0)) return lfail(PS_ERR_ARG, "Hamiltonian with zero one-norm");
     if (!(C > 0.0)) return lfail(PS_ERR_ARG, "Hamiltonian whose terms all commute (bound 0): no Trotter error");
     if (int rc = ham_coefficient(ham, idx, amp, ndet)) return rc;
-    query_features(ham->H, C, std::hypot(ham->k_re, ham->k_im), t, r, out);
+    query_features(ham->H, C, std::hypot(ham->k_re, ham->k_im), ham->e2_norm2, t, r, out);
     return PS_OK;
 }
 
@@ -208,6 +268,7 @@ int ps_ham_error_coefficient(ps_ham *ham, const uint64_t *idx, const double *amp
     if (int rc = ham_coefficient(ham, idx, amp, ndet)) return rc;
     out[0] = ham->k_re;
     out[1] = ham->k_im;
+    out[2] = ham->e2_norm2;
     return PS_OK;
 }
 

@@ -99,16 +99,27 @@ def jw_hamiltonian(n: int, L: int, seed: int, lam: float | None = None, p_two_qu
     return xs, zs, hs
 
 
-def determinant_state(n: int, seed: int, ndet: int = 8):
-    """Sparse state: (indices, complex amplitudes) of `ndet` distinct half-filled basis states."""
+def determinant_state(n: int, seed: int, ndet: int = 8, min_distance: int = 0):
+    """Sparse state: (indices, complex amplitudes) of `ndet` distinct half-filled
+    basis states, pairwise at Hamming distance >= min_distance when given."""
     rng = np.random.default_rng(seed)
     weight = n // 2
     idx: list[int] = []
+    attempts = 0
+    restarts = 0
     while len(idx) < ndet:
+        attempts += 1
+        if attempts > 5000:
+            # the determinants drawn so far leave no room: start the set again
+            restarts += 1
+            if restarts > 100:
+                raise ValueError(f"cannot draw {ndet} determinants of {n} qubits at distance >= {min_distance}")
+            idx, attempts = [], 0
         bits = rng.choice(n, size=weight, replace=False)
         k = int(sum(1 << int(b) for b in bits))
-        if k not in idx:
-            idx.append(k)
+        if k in idx or any(bin(k ^ j).count("1") < min_distance for j in idx):
+            continue
+        idx.append(k)
     amp = rng.standard_normal(ndet) + 1j * rng.standard_normal(ndet)
     amp /= np.sqrt(np.sum(np.abs(amp) ** 2))
     return np.array(idx, dtype=np.uint64), amp

@@ -39,27 +39,33 @@ def richardson3(g32: complex, g64: complex, g128: complex) -> complex:
     return (8.0 * g128 - 6.0 * g64 + g32) / 3.0
 
 
-def initial_state(n: int, seed: int, dtype, device):
-    """The 8-determinant guiding state on the device (Methods: a few leading
+def initial_state(n: int, seed: int, dtype, device, min_distance: int = 0, ndet: int = 8):
+    """The few-determinant guiding state on the device (Methods: a few leading
     determinants stand in for the ground state)."""
     import torch
 
     from . import inputs
-    idx, amp = inputs.determinant_state(n, seed=seed)
+    idx, amp = inputs.determinant_state(n, seed=seed, ndet=ndet, min_distance=min_distance)
     t = torch.zeros(1 << n, dtype=dtype, device=device)
     t[torch.as_tensor(idx.astype(np.int64), device=device)] = torch.as_tensor(amp, device=device).to(dtype)
     return t
 
 
 class Problem:
-    """One Hamiltonian with its initial state (8 determinants from a seed)."""
+    """One Hamiltonian with its initial state (ndet determinants from a seed,
+    optionally pairwise at Hamming distance >= min_distance)."""
 
-    def __init__(self, n: int, x, z, h, psi_seed: int):
+    def __init__(self, n: int, x, z, h, psi_seed: int, min_distance: int = 0, ndet: int = 8):
         from . import inputs
         self.n, self.x, self.z, self.h = n, np.asarray(x, np.uint64), np.asarray(z, np.uint64), np.asarray(h)
         self.psi_seed = psi_seed
+        self.min_distance = min_distance
+        self.ndet = ndet
         self.ham = Hamiltonian(n, self.x, self.z, self.h)
-        self.det_idx, self.det_amp = inputs.determinant_state(n, seed=psi_seed)
+        self.det_idx, self.det_amp = inputs.determinant_state(n, seed=psi_seed, ndet=ndet, min_distance=min_distance)
+
+    def state(self, dtype, device="cuda"):
+        return initial_state(self.n, self.psi_seed, dtype, device, self.min_distance, self.ndet)
 
     def features(self, t: float, r: int):
         return self.ham.features(self.det_idx, self.det_amp, t, r)
@@ -69,10 +75,15 @@ class Problem:
         return len(self.h)
 
 
-def synthetic_problems(count: int, seed: int, n_range=(14, 22), L_range=(200, 2000), lam_range=None):
+def synthetic_problems(count: int, seed: int, n_range=(14, 22), L_range=(200, 2000), lam_range=None,
+                       far_every: int = 0, far_distance: int = 10):
     """Seeded JW-like Hamiltonians: n uniform in n_range, L uniform in
     L_range, one-norm uniform in lam_range (default: the generator's
-    L-dependent one-norm)."""
+    L-dependent one-norm).  With far_every = k, every k-th problem has at
+    least 16 qubits and a guiding state of four determinants pairwise at
+    Hamming distance >= far_distance, so that no product of two 2- or 4-qubit
+    terms connects them (the first-order error coefficient vanishes, as it
+    does for eight-determinant states at large n)."""
     from . import inputs
     rng = np.random.default_rng(seed)
     out = []
@@ -80,8 +91,12 @@ def synthetic_problems(count: int, seed: int, n_range=(14, 22), L_range=(200, 20
         n = int(rng.integers(n_range[0], n_range[1] + 1))
         L = int(rng.integers(L_range[0], L_range[1] + 1))
         lam = None if lam_range is None else float(rng.uniform(lam_range[0], lam_range[1]))
+        far = far_every and i % far_every == far_every - 1
+        if far:
+            n = max(n, 16)
         x, z, h = inputs.jw_hamiltonian(n, L, seed=seed * 7919 + i, lam=lam)
-        out.append(Problem(n, x, z, h, psi_seed=seed * 7919 + i))
+        out.append(Problem(n, x, z, h, psi_seed=seed * 7919 + i, min_distance=far_distance if far else 0,
+                           ndet=4 if far else 8))
     return out
 
 
@@ -109,7 +124,7 @@ def overlaps_by_batch(problems, times, r_values, dtype=None, cfg=None, max_rotat
         for pi, ti, r in chunk:
             p = problems[pi]
             if pi not in psi0:
-                psi0[pi] = initial_state(p.n, p.psi_seed, dtype, device)
+                psi0[pi] = p.state(dtype, device)
             x, z, phi = p.ham.trotter_stream(times[ti], r)
             runs.append(dict(n=p.n, x=x, z=z, phi=phi, psi0=psi0[pi]))
         b = Batch(runs, dtype=dtype, cfg=cfg, device=device)
@@ -256,7 +271,7 @@ def sweep(problem: Problem, t: float, eps: float = 1e-3, r_max: int = 4096, dtyp
     """The plain doubling sweep on one GPU state: (r, rotations applied, g_r)."""
     import torch
     dtype = torch.complex64 if dtype is None else dtype
-    psi0 = StateVector(problem.n, tensor=initial_state(problem.n, problem.psi_seed, dtype, "cuda"))
+    psi0 = StateVector(problem.n, tensor=problem.state(dtype))
     work = StateVector(problem.n, dtype=dtype)
     try:
         return ps_trotter_sweep(work.handle, psi0.handle, problem.ham.handle, t, eps, r_max)
@@ -276,7 +291,7 @@ def run_error(problem: Problem, t: float, r: int, g_ref: complex, dtype=None) ->
     """|g_r - g_ref| for one Trotter run on the GPU."""
     import torch
     dtype = torch.complex64 if dtype is None else dtype
-    psi0 = StateVector(problem.n, tensor=initial_state(problem.n, problem.psi_seed, dtype, "cuda"))
+    psi0 = StateVector(problem.n, tensor=problem.state(dtype))
     work = StateVector(problem.n, dtype=dtype)
     try:
         work.copy_from(psi0)

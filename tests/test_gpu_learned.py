@@ -144,7 +144,9 @@ def test_features_and_bound_match_oracle():
         idx, amp = inputs.determinant_state(n, seed=seed + 10)
         psi = inputs.densify(n, idx, amp)
         H = ps.Hamiltonian(n, x, z, h)
-        assert abs(H.error_coefficient(idx, amp) - OL.error_coefficient(n, x, z, h, psi)) < 1e-12
+        K, e2 = H.error_coefficient(idx, amp)
+        assert abs(K - OL.error_coefficient(n, x, z, h, psi)) < 1e-12
+        assert e2 == pytest.approx(OL.second_order_norm2(n, x, z, h, psi), rel=1e-12)
         for t, r in ((0.1, 1), (1.3, 7), (3.2, 64)):
             assert np.allclose(H.features(idx, amp, t, r), OL.features(n, x, z, h, t, r, psi), rtol=3e-7, atol=1e-6)
         for L_D in (0, L // 10, L):

@@ -73,9 +73,13 @@ def test_features_hand_example():
     C = 4 * (0.5 * 0.25 + 0.25 * (0.5 + 0.25) + 0.25 * 0.25)
     # K on |00>: pair (X1, Z1Z2): h2 h1 <00|Z1Z2 X1|00> = 0 (X1 flips qubit 1);
     # pair (Z1Z2, Y2): h3 h2 <00|Y2 Z1Z2|00> = 0 (Y2 flips qubit 2)
-    expect = [C / 4, math.log(3), math.log(lam), math.log(0.5), math.log(t), math.log(r), math.log(C),
-              math.log(C * t * t / r), 0.25, math.log(0.5 * 1 + 0.25 * 2 + 0.25 * 1), math.log(L.K_FLOOR),
-              math.log(L.K_FLOOR) + 2 * math.log(t) - math.log(r)]
+    expect = [math.log(3), math.log(lam), math.log(0.5), math.log(t), math.log(r), math.log(C),
+              math.log(C * t * t / r), 0.25, math.log(L.K_FLOOR)]
+    # E2 |00> = -(h2 h1 Z1Z2 X1 + h3 h2 Y2 Z1Z2)|00>: Z1Z2 X1|00> = Z1Z2|01> = -|01> (qubit 1 set),
+    # Y2 Z1Z2|00> = Y2|00> = i|10>; so E2|00> = -(-0.125 * -1)|01> - (-0.0625 i)|10>
+    n2 = 0.125 ** 2 + 0.0625 ** 2
+    # K = 0 on |00>: the estimate is the second-order one alone
+    expect += [math.log(n2), math.log(n2 * t ** 4 / (2 * r * r)), 0.0]
     assert np.allclose(f, expect, rtol=1e-14, atol=1e-15)
 
 
@@ -97,6 +101,8 @@ def test_error_coefficient_dense_and_small_time_limit():
             Kd += h[l] * h[k] * np.vdot(psi, (P[l] @ P[k] - P[k] @ P[l]) @ psi) / 2
     K = L.error_coefficient(n, x, z, h, psi)
     assert abs(K - Kd) < 1e-13
+    E2 = sum(-0.5 * h[l] * h[k] * (P[l] @ P[k] - P[k] @ P[l]) for k in range(len(h)) for l in range(k + 1, len(h)))
+    assert L.second_order_norm2(n, x, z, h, psi) == pytest.approx(np.linalg.norm(E2 @ psi) ** 2, rel=1e-13)
     H = sum(hv * Pm for hv, Pm in zip(h, P))
     for r in (1, 3):
         t = 2e-3
