@@ -173,6 +173,19 @@ def kernel_traffic():
 
 # --------------------------------------------------------------- workload
 
+def aggregate_ranks(dist, device, elapsed_ms: float, units: int, launches: int):
+    """Whole-job numbers of a replica run: the slowest rank's time, and the
+    units and kernel launches summed over ranks (identity without dist)."""
+    if dist is None:
+        return elapsed_ms, units, launches
+    import torch
+    tt = torch.tensor([elapsed_ms], device=device, dtype=torch.float64)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    tr = torch.tensor([units, launches], device=device, dtype=torch.float64)
+    dist.all_reduce(tr)
+    return float(tt.item()), int(tr[0].item()), int(tr[1].item())
+
+
 def make_workload(rank: int):
     from paper_2504_17881_gb300 import inputs
     x, z, h = inputs.jw_hamiltonian(N_QUBITS, N_TERMS, seed=HAM_SEED)
@@ -264,16 +277,7 @@ def run_ours(args):
     stats = psi.stats()
     rotations = args.steps * SEG_LEN
 
-    t_max = elapsed_ms
-    tot_rot = rotations
-    launches = sum(stats["launches"].values())
-    if dist is not None:
-        tt = torch.tensor([elapsed_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_max = float(tt.item())
-        tr = torch.tensor([rotations, launches], device=dev, dtype=torch.float64)
-        dist.all_reduce(tr)
-        tot_rot, launches = int(tr[0].item()), int(tr[1].item())
+    t_max, tot_rot, launches = aggregate_ranks(dist, dev, elapsed_ms, rotations, sum(stats["launches"].values()))
     value = tot_rot / (t_max / 1e3)
 
     # roofline of the dominant kernel (fused tile kernel), timed live with events
@@ -485,13 +489,9 @@ def run_batched(args):
     g64 = b.wait()
     clock_info = clocks.stop()
     ms = ev0.elapsed_time(ev1)
-    t_max = ms
-    if dist is not None:
-        tt = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_max = float(tt.item())
     rot_per_launch = info["rotations"]
-    value = world * args.steps * rot_per_launch / (t_max / 1e3)
+    t_max, tot_rot, _ = aggregate_ranks(dist, dev, ms, args.steps * rot_per_launch, args.steps)
+    value = tot_rot / (t_max / 1e3)
     amp_updates = world * args.steps * info["amplitude_rotations"] / (t_max / 1e3)
     pass_bytes = 2.0 * 8.0 * info["amplitude_passes"]
     achieved = pass_bytes / (ms / args.steps / 1e3) / 1e9
