@@ -53,6 +53,8 @@ def _load():
         "or_partial_split": (i32, [sz, vp, sz, vp]),
         "or_partial": (i32, [i32, vp, vp, sz, vp, vp, vp, sz, f64, u32, u64, u64]),
         "or_partial_sample_count": (u64, [f64, f64, i32]),
+        "or_trotter2": (i32, [i32, vp, vp, sz, vp, vp, vp, f64, u32]),
+        "or_partial2": (i32, [i32, vp, vp, sz, vp, vp, vp, sz, f64, u32, u64, u64]),
         "or_amplitudes_sparse": (i32, [i32, sz, vp, vp, vp, vp, vp, sz, sz, vp, vp]),
     }
     for name, (res, args) in sig.items():
@@ -142,6 +144,28 @@ def trotter(psi, x, z, h, t: float, r: int) -> np.ndarray:
     return a
 
 
+def trotter2(psi, x, z, h, t: float, r: int) -> np.ndarray:
+    """Second-order symmetric product formula (each factor written out)."""
+    a = _state(psi)
+    x, z, h = _u64(x), _u64(z), _f64(h)
+    tmp = np.empty_like(a)
+    _check(_load().or_trotter2(a.size.bit_length() - 1, _p(a), _p(tmp), x.size, _p(x), _p(z), _p(h),
+                               float(t), int(r)), "trotter2")
+    return a
+
+
+def lexicographic_order(n: int, x, z) -> list[int]:
+    """Term indices sorted by their Pauli strings read from qubit n down to
+    qubit 1, letters ordered I < X < Y < Z (ties keep input order)."""
+    letter = {(0, 0): "0", (1, 0): "1", (1, 1): "2", (0, 1): "3"}
+
+    def key(l):
+        xv, zv = int(x[l]), int(z[l])
+        return "".join(letter[((xv >> q) & 1, (zv >> q) & 1)] for q in reversed(range(n)))
+
+    return sorted(range(len(x)), key=lambda l: (key(l), l))
+
+
 def splitmix64(seed: int, count: int) -> np.ndarray:
     st = np.array([seed], dtype=np.uint64)
     lib = _load()
@@ -177,6 +201,16 @@ def partial(psi, x, z, h, L_D: int, t: float, r: int, Ns: int, seed: int) -> np.
     tmp = np.empty_like(a)
     _check(_load().or_partial(a.size.bit_length() - 1, _p(a), _p(tmp), x.size, _p(x), _p(z), _p(h),
                               int(L_D), float(t), int(r), int(Ns), int(seed)), "partial")
+    return a
+
+
+def partial2(psi, x, z, h, L_D: int, t: float, r: int, Ns: int, seed: int) -> np.ndarray:
+    """Second-order partially randomised steps (deterministic halves around 2 Ns draws)."""
+    a = _state(psi)
+    x, z, h = _u64(x), _u64(z), _f64(h)
+    tmp = np.empty_like(a)
+    _check(_load().or_partial2(a.size.bit_length() - 1, _p(a), _p(tmp), x.size, _p(x), _p(z), _p(h),
+                               int(L_D), float(t), int(r), int(Ns), int(seed)), "partial2")
     return a
 
 

@@ -166,6 +166,29 @@ int or_trotter(int n, cplx *psi, cplx *tmp, size_t L, const uint64_t *x, const u
     return 0;
 }
 
+/* Second-order (symmetric) product formula: each of r steps of delta = t/r
+ * applies exp(i (delta/2) h_l P_l) for l = 1..L and then for l = L..1
+ * (Methods: "This work uses the second-order variant"; the standard
+ * symmetric splitting).  Written out factor by factor, without merging
+ * the adjacent equal factors. */
+int or_trotter2(int n, cplx *psi, cplx *tmp, size_t L, const uint64_t *x, const uint64_t *z,
+                const double *h, double t, uint32_t r)
+{
+    if (r == 0) return -1;
+    double half = 0.5 * (t / (double)r);
+    for (uint32_t step = 0; step < r; ++step) {
+        for (size_t l = 0; l < L; ++l) {
+            int rc = or_rotate(n, psi, tmp, x[l], z[l], half * h[l]);
+            if (rc) return rc;
+        }
+        for (size_t l = L; l-- > 0;) {
+            int rc = or_rotate(n, psi, tmp, x[l], z[l], half * h[l]);
+            if (rc) return rc;
+        }
+    }
+    return 0;
+}
+
 /* SplitMix64 (Steele, Lea & Flood 2014): state += 0x9e3779b97f4a7c15, then
  * the published two-multiply finaliser.  Counter-based: the j-th output
  * (j = 1, 2, ...) depends only on seed + j * 0x9e3779b97f4a7c15. */
@@ -291,6 +314,49 @@ int or_partial(int n, cplx *psi, cplx *tmp, size_t L, const uint64_t *x, const u
             size_t l = rest[m];
             rc = or_rotate(n, psi, tmp, x[l], z[l], h[l] > 0.0 ? tau : -tau);
         }
+    }
+    free(cdf);
+    free(is_det);
+    free(rest);
+    return rc;
+}
+
+/* Second-order partially randomised step (the reading used here; the
+ * paper states only that the randomised part takes twice the samples per
+ * step at second order, Methods): per step of delta = t/r, the
+ * deterministic terms forward with delta/2, then 2 Ns draws from H_R each
+ * with angle sgn(h) lambda_R delta / (2 Ns), then the deterministic terms
+ * backward with delta/2.  One SplitMix64 stream runs through all steps. */
+int or_partial2(int n, cplx *psi, cplx *tmp, size_t L, const uint64_t *x, const uint64_t *z,
+                const double *h, size_t L_D, double t, uint32_t r, uint64_t Ns, uint64_t seed)
+{
+    if (r == 0 || L_D > L) return -1;
+    unsigned char *is_det = (unsigned char *)malloc(L ? L : 1);
+    size_t *rest = (size_t *)malloc((L ? L : 1) * sizeof(size_t));
+    if (!is_det || !rest) { free(is_det); free(rest); return -2; }
+    or_partial_split(L, h, L_D, is_det);
+    size_t LR = 0;
+    for (size_t l = 0; l < L; ++l)
+        if (!is_det[l]) rest[LR++] = l;
+    double *cdf = make_cdf(LR, h, rest);
+    if (!cdf) { free(is_det); free(rest); return -2; }
+    double lambda_R = LR ? cdf[LR - 1] : 0.0;
+    double delta = t / (double)r;
+    int sample = (LR > 0 && Ns > 0 && lambda_R > 0.0);
+    double tau = sample ? lambda_R * delta / (double)(2 * Ns) : 0.0;
+    uint64_t state = seed;
+    int rc = 0;
+    for (uint32_t step = 0; step < r && !rc; ++step) {
+        for (size_t l = 0; l < L && !rc; ++l)
+            if (is_det[l]) rc = or_rotate(n, psi, tmp, x[l], z[l], 0.5 * delta * h[l]);
+        if (sample)
+            for (uint64_t j = 0; j < 2 * Ns && !rc; ++j) {
+                size_t m = draw_term(cdf, LR, &state);
+                size_t l = rest[m];
+                rc = or_rotate(n, psi, tmp, x[l], z[l], h[l] > 0.0 ? tau : -tau);
+            }
+        for (size_t l = L; l-- > 0 && !rc;)
+            if (is_det[l]) rc = or_rotate(n, psi, tmp, x[l], z[l], 0.5 * delta * h[l]);
     }
     free(cdf);
     free(is_det);

@@ -353,3 +353,87 @@ def test_trotter_term_order_first_term_acts_first():
     got = oracle.trotter(psi, x, z, h, t, 1)
     assert np.max(np.abs(got - ref)) < 1e-14
     assert np.max(np.abs(got - wrong)) > 1e-3
+
+
+# ------------------------------------------------------------ second order
+
+def test_trotter2_exact_for_commuting_terms():
+    n = 4
+    terms = ["XXII", "YYII", "ZZII", "IIXX", "IIZZ"]
+    xz = [oracle.pauli_from_string(s) for s in terms]
+    x = [a for a, _ in xz]
+    z = [b for _, b in xz]
+    h = [0.7, -0.4, 1.1, 0.3, -0.9]
+    psi = inputs.gaussian_state(n, 19)
+    ref = expm_herm(dense_ham(n, x, z, h), 0.8) @ psi
+    for r in (1, 2, 5):
+        assert np.max(np.abs(oracle.trotter2(psi, x, z, h, 0.8, r) - ref)) < 1e-13
+
+
+def test_trotter2_second_order_convergence_rate():
+    n = 6
+    x, z, h = inputs.jw_hamiltonian(n, 24, seed=12)
+    psi = inputs.gaussian_state(n, 13)
+    ref = expm_herm(dense_ham(n, x, z, h), 1.0) @ psi
+    rs = np.array([4, 8, 16, 32, 64])
+    errs = np.array([np.linalg.norm(oracle.trotter2(psi, x, z, h, 1.0, int(r)) - ref) for r in rs])
+    slope = np.polyfit(np.log(rs), np.log(errs), 1)[0]
+    assert -2.1 < slope < -1.9, (slope, errs)
+
+
+def test_trotter2_is_time_symmetric():
+    # S2(-delta) = S2(delta)^-1 for the symmetric splitting; a first-order
+    # product (or a second half in the wrong order) fails this
+    n = 5
+    x, z, h = inputs.jw_hamiltonian(n, 14, seed=21)
+    psi = inputs.gaussian_state(n, 22)
+    fwd = oracle.trotter2(psi, x, z, h, 0.9, 3)
+    back = oracle.trotter2(fwd, x, z, h, -0.9, 3)
+    assert np.max(np.abs(back - psi)) < 1e-13
+    back1 = oracle.trotter(oracle.trotter(psi, x, z, h, 0.9, 3), x, z, h, -0.9, 3)
+    assert np.max(np.abs(back1 - psi)) > 1e-3
+
+
+def test_partial2_reduces_to_trotter2_and_qdrift():
+    n = 5
+    x, z, h = inputs.jw_hamiltonian(n, 10, seed=31)
+    psi = inputs.gaussian_state(n, 32)
+    a = oracle.partial2(psi, x, z, h, L_D=10, t=0.7, r=3, Ns=5, seed=1)
+    assert np.array_equal(a, oracle.trotter2(psi, x, z, h, 0.7, 3))
+    # no deterministic part, one step: 2 Ns draws over time t, i.e. qDRIFT with N = 2 Ns
+    a = oracle.partial2(psi, x, z, h, L_D=0, t=0.7, r=1, Ns=17, seed=9)
+    assert np.array_equal(a, oracle.qdrift(psi, x, z, h, 0.7, 34, seed=9))
+
+
+def test_partial2_mean_matches_exact_expectation():
+    n = 4
+    x, z, h = inputs.jw_hamiltonian(n, 8, seed=41)
+    psi = inputs.gaussian_state(n, 43)
+    L_D, t, r, Ns, S = 3, 0.8, 2, 2, 3000
+    det = oracle.partial_split(h, L_D)
+    half = 0.5 * t / r
+    fwd = np.eye(1 << n, dtype=complex)
+    for l in range(h.size):
+        if det[l]:
+            fwd = expm_herm(dense_pauli(n, int(x[l]), int(z[l])), half * h[l]) @ fwd
+    bwd = np.eye(1 << n, dtype=complex)
+    for l in reversed(range(h.size)):
+        if det[l]:
+            bwd = expm_herm(dense_pauli(n, int(x[l]), int(z[l])), half * h[l]) @ bwd
+    hr = np.where(det, 0.0, h)
+    lam_r = np.abs(hr).sum()
+    tau = lam_r * (t / r) / (2 * Ns)
+    m = math.cos(tau) * np.eye(1 << n) + 1j * math.sin(tau) * dense_ham(n, x, z, hr) / lam_r
+    step = bwd @ np.linalg.matrix_power(m, 2 * Ns) @ fwd
+    want = np.vdot(psi, np.linalg.matrix_power(step, r) @ psi)
+    g = np.array([np.vdot(psi, oracle.partial2(psi, x, z, h, L_D, t, r, Ns, seed=s)) for s in range(S)])
+    band = 5 * (np.std(g.real) + np.std(g.imag)) / math.sqrt(S)
+    assert abs(g.mean() - want) < band, (g.mean(), want, band)
+
+
+def test_lexicographic_order_hand_example():
+    # strings written qubit 1 first; the order reads them from qubit n down, I < X < Y < Z
+    terms = ["XZ", "ZI", "IY", "YY"]
+    xz = [oracle.pauli_from_string(s) for s in terms]
+    order = oracle.lexicographic_order(2, [a for a, _ in xz], [b for _, b in xz])
+    assert order == [1, 2, 3, 0]
