@@ -261,6 +261,33 @@ int ps_evolve_qdrift(ps_state *st, const ps_ham *ham, double t, uint64_t N, uint
 int ps_evolve_partial(ps_state *st, const ps_ham *ham, size_t L_D, double t, uint32_t r, uint64_t Ns,
                       uint64_t seed);
 
+/* Second order (Methods: the paper's runs use the second-order variant).
+ * ps_evolve_trotter2: r symmetric steps of delta = t/r, each applying the
+ * terms l = 1..L with angle (delta/2) h_l and then l = L..1 with (delta/2) h_l.
+ * The two middle factors of a step and the factors that meet between steps
+ * are the same string and are applied as one rotation, so r steps of L
+ * terms are r (2L - 2) + 1 rotations (ps_trotter2_length; 1 for L = 1).
+ * ps_evolve_partial2: per step, the first L_D terms by decreasing |h|
+ * forward with delta/2, then 2 Ns qDRIFT draws from the rest with angle
+ * sgn(h) lambda_R delta / (2 Ns), then the same L_D terms backward with
+ * delta/2 (the paper fixes only that the randomised part takes twice the
+ * samples per step at second order; this symmetric form is the reading
+ * used).  It reduces to ps_evolve_trotter2 for L_D = L and to qDRIFT with
+ * 2 Ns samples for L_D = 0, r = 1.  Streams as for the first-order calls. */
+int ps_evolve_trotter2(ps_state *st, const ps_ham *ham, double t, uint32_t r);
+int ps_evolve_partial2(ps_state *st, const ps_ham *ham, size_t L_D, double t, uint32_t r, uint64_t Ns,
+                       uint64_t seed);
+uint64_t ps_trotter2_length(const ps_ham *ham, uint32_t r);
+int ps_trotter2_stream(const ps_ham *ham, double t, uint32_t r, uint64_t *x_out, uint64_t *z_out, double *phi_out);
+uint64_t ps_partial2_length(const ps_ham *ham, size_t L_D, uint32_t r, uint64_t Ns);
+int ps_partial2_stream(const ps_ham *ham, size_t L_D, double t, uint32_t r, uint64_t Ns, uint64_t seed,
+                       uint64_t *x_out, uint64_t *z_out, double *phi_out);
+/* Reorder the terms in place by their Pauli strings read from qubit n down
+ * to qubit 1, letters I < X < Y < Z, ties in input order (Methods:
+ * deterministic terms are ordered lexicographically, so strings that share
+ * their upper qubits are applied together). */
+int ps_ham_sort_lexicographic(ps_ham *ham);
+
 /* ------------------------------------------------------------ statistics */
 
 /* Counters since creation or the last reset; synchronises the stream when

@@ -23,7 +23,8 @@ from ._lib import (PS_C64, PS_C128, PS_ERR_ARG, PS_ERR_TIMEOUT, PsError, ps_abi_
                    ps_mlp_num_params, ps_mlp_get_params, ps_mlp_set_params, ps_mlp_get_grads,
                    ps_mlp_set_normalization, ps_mlp_get_normalization, ps_mlp_fit_normalization, ps_mlp_loss_grad,
                    ps_mlp_adam_step, ps_mlp_train, ps_mlp_predict, ps_mlp_pick_r,
-                   ps_mlp_pick_r_ensemble)
+                   ps_mlp_pick_r_ensemble, ps_evolve_trotter2, ps_evolve_partial2, ps_trotter2_length,
+                   ps_trotter2_stream, ps_partial2_length, ps_partial2_stream, ps_ham_sort_lexicographic)
 
 __all__ = [n for n in dir(_lib) if n.startswith("ps_")] + ["StateVector", "Hamiltonian", "Plan", "Batch",
                                                               "PsError", "PS_C64", "PS_C128"]
@@ -108,6 +109,12 @@ class StateVector:
     def evolve_partial(self, ham: "Hamiltonian", L_D: int, t: float, r: int, Ns: int, seed: int):
         ps_evolve_partial(self.handle, ham.handle, L_D, t, r, Ns, seed)
 
+    def evolve_trotter2(self, ham: "Hamiltonian", t: float, r: int):
+        ps_evolve_trotter2(self.handle, ham.handle, t, r)
+
+    def evolve_partial2(self, ham: "Hamiltonian", L_D: int, t: float, r: int, Ns: int, seed: int):
+        ps_evolve_partial2(self.handle, ham.handle, L_D, t, r, Ns, seed)
+
     def norm2(self) -> float:
         return ps_norm(self.handle)
 
@@ -133,6 +140,16 @@ class Hamiltonian:
 
     def trotter_stream(self, t: float, r: int):
         return ps_trotter_stream(self.handle, self.L, t, r)
+
+    def trotter2_stream(self, t: float, r: int):
+        return ps_trotter2_stream(self.handle, t, r)
+
+    def partial2_stream(self, L_D: int, t: float, r: int, Ns: int, seed: int):
+        return ps_partial2_stream(self.handle, L_D, t, r, Ns, seed)
+
+    def sort_lexicographic(self):
+        """Reorder the terms in place (upper qubits first, I < X < Y < Z)."""
+        ps_ham_sort_lexicographic(self.handle)
 
     def trotter_bound(self, L_D: int | None = None) -> float:
         return ps_ham_trotter_bound(self.handle, self.L if L_D is None else L_D)

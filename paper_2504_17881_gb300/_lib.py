@@ -121,6 +121,13 @@ _SIGS = {
     "ps_batch_destroy": (None, [_vp]),
     "ps_batch_describe": (_i, [_i, ctypes.POINTER(ps_run_desc), _sz, ctypes.POINTER(ps_batch_config), _i, _i,
                                ctypes.POINTER(ps_batch_info), _vp, _vp, _vp]),
+    "ps_evolve_trotter2": (_i, [_vp, _vp, _d, _u32]),
+    "ps_evolve_partial2": (_i, [_vp, _vp, _sz, _d, _u32, _u64, _u64]),
+    "ps_trotter2_length": (_u64, [_vp, _u32]),
+    "ps_trotter2_stream": (_i, [_vp, _d, _u32, _vp, _vp, _vp]),
+    "ps_partial2_length": (_u64, [_vp, _sz, _u32, _u64]),
+    "ps_partial2_stream": (_i, [_vp, _sz, _d, _u32, _u64, _u64, _vp, _vp, _vp]),
+    "ps_ham_sort_lexicographic": (_i, [_vp]),
     "ps_ham_trotter_bound": (_i, [_vp, _sz, ctypes.POINTER(_d)]),
     "ps_ham_features": (_i, [_vp, _vp, _vp, _sz, _d, _u32, _vp]),
     "ps_ham_error_coefficient": (_i, [_vp, _vp, _vp, _sz, _vp]),
@@ -603,3 +610,43 @@ def ps_mlp_pick_r_ensemble(nets, ham: int, idx, amp, t: float, eps: float, margi
     if rc not in (PS_OK, PS_ERR_UNSUPPORTED):
         _check(rc)
     return int(r.value), pred
+
+
+# ------------------------------------------------------------- second order
+
+def ps_evolve_trotter2(h: int, ham: int, t: float, r: int):
+    _check(lib.ps_evolve_trotter2(ctypes.c_void_p(h), ctypes.c_void_p(ham), t, r))
+
+
+def ps_evolve_partial2(h: int, ham: int, L_D: int, t: float, r: int, Ns: int, seed: int):
+    _check(lib.ps_evolve_partial2(ctypes.c_void_p(h), ctypes.c_void_p(ham), L_D, t, r, Ns, seed))
+
+
+def ps_trotter2_length(ham: int, r: int) -> int:
+    return int(lib.ps_trotter2_length(ctypes.c_void_p(ham), r))
+
+
+def ps_trotter2_stream(ham: int, t: float, r: int):
+    m = ps_trotter2_length(ham, r)
+    x = np.zeros(m, dtype=np.uint64)
+    z = np.zeros(m, dtype=np.uint64)
+    phi = np.zeros(m, dtype=np.float64)
+    _check(lib.ps_trotter2_stream(ctypes.c_void_p(ham), t, r, _ptr(x), _ptr(z), _ptr(phi)))
+    return x, z, phi
+
+
+def ps_partial2_length(ham: int, L_D: int, r: int, Ns: int) -> int:
+    return int(lib.ps_partial2_length(ctypes.c_void_p(ham), L_D, r, Ns))
+
+
+def ps_partial2_stream(ham: int, L_D: int, t: float, r: int, Ns: int, seed: int):
+    m = ps_partial2_length(ham, L_D, r, Ns)
+    x = np.zeros(m, dtype=np.uint64)
+    z = np.zeros(m, dtype=np.uint64)
+    phi = np.zeros(m, dtype=np.float64)
+    _check(lib.ps_partial2_stream(ctypes.c_void_p(ham), L_D, t, r, Ns, seed, _ptr(x), _ptr(z), _ptr(phi)))
+    return x, z, phi
+
+
+def ps_ham_sort_lexicographic(ham: int):
+    _check(lib.ps_ham_sort_lexicographic(ctypes.c_void_p(ham)))

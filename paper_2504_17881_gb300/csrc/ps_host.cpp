@@ -615,6 +615,70 @@ int ps_evolve_partial(ps_state *st, const ps_ham *ham, size_t L_D, double t, uin
     return run_sequence(st, s.x.data(), s.z.data(), s.phi.data(), s.size());
 }
 
+int ps_evolve_trotter2(ps_state *st, const ps_ham *ham, double t, uint32_t r) {
+    if (int rc = check_state(st)) return rc;
+    if (!ham) return fail(PS_ERR_ARG, "null Hamiltonian");
+    if (ham->H.n != st->n) return fail(PS_ERR_ARG, "Hamiltonian and state differ in n");
+    if (r == 0) return fail(PS_ERR_ARG, "r must be >= 1");
+    Stream s;
+    trotter2_stream(ham->H, t, r, s);
+    DeviceGuard g(st->device);
+    return run_sequence(st, s.x.data(), s.z.data(), s.phi.data(), s.size());
+}
+
+int ps_evolve_partial2(ps_state *st, const ps_ham *ham, size_t L_D, double t, uint32_t r, uint64_t Ns,
+                       uint64_t seed) {
+    if (int rc = check_state(st)) return rc;
+    if (!ham) return fail(PS_ERR_ARG, "null Hamiltonian");
+    if (ham->H.n != st->n) return fail(PS_ERR_ARG, "Hamiltonian and state differ in n");
+    if (r == 0) return fail(PS_ERR_ARG, "r must be >= 1");
+    if (L_D > ham->H.h.size()) return fail(PS_ERR_ARG, "L_D exceeds the number of terms");
+    Stream s;
+    partial2_stream(ham->H, L_D, t, r, Ns, seed, s);
+    DeviceGuard g(st->device);
+    return run_sequence(st, s.x.data(), s.z.data(), s.phi.data(), s.size());
+}
+
+uint64_t ps_trotter2_length(const ps_ham *ham, uint32_t r) { return ham ? trotter2_length(ham->H.h.size(), r) : 0; }
+
+int ps_trotter2_stream(const ps_ham *ham, double t, uint32_t r, uint64_t *x_out, uint64_t *z_out, double *phi_out) {
+    if (!ham) return fail(PS_ERR_ARG, "null Hamiltonian");
+    if (r == 0) return fail(PS_ERR_ARG, "r must be >= 1");
+    Stream s;
+    trotter2_stream(ham->H, t, r, s);
+    if (s.size() && (!x_out || !z_out || !phi_out)) return fail(PS_ERR_ARG, "null output array");
+    std::copy(s.x.begin(), s.x.end(), x_out);
+    std::copy(s.z.begin(), s.z.end(), z_out);
+    std::copy(s.phi.begin(), s.phi.end(), phi_out);
+    return PS_OK;
+}
+
+uint64_t ps_partial2_length(const ps_ham *ham, size_t L_D, uint32_t r, uint64_t Ns) {
+    if (!ham || L_D > ham->H.h.size()) return 0;
+    return partial2_length(ham->H, L_D, r, Ns);
+}
+
+int ps_partial2_stream(const ps_ham *ham, size_t L_D, double t, uint32_t r, uint64_t Ns, uint64_t seed,
+                       uint64_t *x_out, uint64_t *z_out, double *phi_out) {
+    if (!ham) return fail(PS_ERR_ARG, "null Hamiltonian");
+    if (r == 0) return fail(PS_ERR_ARG, "r must be >= 1");
+    if (L_D > ham->H.h.size()) return fail(PS_ERR_ARG, "L_D exceeds the number of terms");
+    Stream s;
+    partial2_stream(ham->H, L_D, t, r, Ns, seed, s);
+    if (s.size() && (!x_out || !z_out || !phi_out)) return fail(PS_ERR_ARG, "null output array");
+    std::copy(s.x.begin(), s.x.end(), x_out);
+    std::copy(s.z.begin(), s.z.end(), z_out);
+    std::copy(s.phi.begin(), s.phi.end(), phi_out);
+    return PS_OK;
+}
+
+int ps_ham_sort_lexicographic(ps_ham *ham) {
+    if (!ham) return fail(PS_ERR_ARG, "null Hamiltonian");
+    lexicographic_sort(ham->H);
+    ham->k_valid = false;  // the error coefficients depend on the term order
+    return PS_OK;
+}
+
 int ps_get_stats(ps_state *st, ps_stats *out) {
     if (int rc = check_state(st)) return rc;
     if (!out) return fail(PS_ERR_ARG, "null output pointer");

@@ -129,4 +129,142 @@ void partial_stream(const Ham &H, size_t L_D, double t, uint32_t r, uint64_t Ns,
     }
 }
 
+// Appends (x, z, phi); merges into the previous rotation when `merge`
+// (the same Pauli string: exp(i a P) exp(i b P) = exp(i (a + b) P)).
+static inline void put(Stream &out, uint64_t x, uint64_t z, double phi, bool merge) {
+    if (merge) {
+        out.phi.back() += phi;
+        return;
+    }
+    out.x.push_back(x);
+    out.z.push_back(z);
+    out.phi.push_back(phi);
+}
+
+// Symmetric second-order steps over the terms `terms` (in that order):
+// forward with delta/2, then backward with delta/2.  The two middle factors
+// of a step and the two factors that meet between steps are the same
+// string and are merged, so r steps of L terms give r (2L - 2) + 1
+// rotations (one rotation for L = 1).
+static void second_order_det(const Ham &H, const std::vector<size_t> &terms, double t, uint32_t r, Stream &out) {
+    const size_t L = terms.size();
+    if (L == 0) return;
+    const double delta = t / (double)r;
+    const double half = 0.5 * delta;
+    if (L == 1) {
+        put(out, H.x[terms[0]], H.z[terms[0]], (double)r * delta * H.h[terms[0]], false);
+        return;
+    }
+    for (uint32_t step = 0; step < r; ++step) {
+        for (size_t i = 0; i < L; ++i) {
+            const size_t l = terms[i];
+            if (i == L - 1)
+                put(out, H.x[l], H.z[l], delta * H.h[l], false);
+            else
+                put(out, H.x[l], H.z[l], half * H.h[l], step > 0 && i == 0);
+        }
+        for (size_t i = L - 1; i-- > 0;) {
+            const size_t l = terms[i];
+            put(out, H.x[l], H.z[l], half * H.h[l], false);
+        }
+    }
+}
+
+uint64_t trotter2_length(size_t L, uint32_t r) {
+    if (L == 0) return 0;
+    if (L == 1) return 1;
+    return (uint64_t)r * (2 * (uint64_t)L - 2) + 1;
+}
+
+void trotter2_stream(const Ham &H, double t, uint32_t r, Stream &out) {
+    std::vector<size_t> all(H.h.size());
+    std::iota(all.begin(), all.end(), 0);
+    out = Stream();
+    out.x.reserve(trotter2_length(all.size(), r));
+    out.z.reserve(out.x.capacity());
+    out.phi.reserve(out.x.capacity());
+    second_order_det(H, all, t, r, out);
+}
+
+uint64_t partial2_length(const Ham &H, size_t L_D, uint32_t r, uint64_t Ns) {
+    std::vector<size_t> det, rest;
+    split_terms(H, L_D, det, rest);
+    double lam_r = 0.0;
+    for (size_t l : rest) lam_r += std::fabs(H.h[l]);
+    const bool sample = !rest.empty() && Ns > 0 && lam_r > 0.0;
+    if (!sample) return trotter2_length(det.size(), r);
+    const uint64_t D = det.size();
+    return (uint64_t)r * (2 * D + 2 * Ns) - (D ? (uint64_t)r - 1 : 0);
+}
+
+// Second-order partially randomised steps: per step of delta = t/r, the
+// deterministic terms forward with delta/2, 2 Ns draws from H_R with angle
+// sgn(h) lambda_R delta / (2 Ns), the deterministic terms backward with
+// delta/2.  The first deterministic factor of a step merges with the last
+// of the step before.  Without draws the steps are second-order Trotter
+// over H_D.
+void partial2_stream(const Ham &H, size_t L_D, double t, uint32_t r, uint64_t Ns, uint64_t seed, Stream &out) {
+    std::vector<size_t> det, rest;
+    split_terms(H, L_D, det, rest);
+    std::vector<double> cdf = running_abs(H.h, rest);
+    const double lam_r = rest.empty() ? 0.0 : cdf.back();
+    const bool sample = !rest.empty() && Ns > 0 && lam_r > 0.0;
+    out = Stream();
+    if (!sample) {
+        second_order_det(H, det, t, r, out);
+        return;
+    }
+    const double delta = t / (double)r;
+    const double half = 0.5 * delta;
+    const double tau = lam_r * delta / (double)(2 * Ns);
+    const uint64_t len = partial2_length(H, L_D, r, Ns);
+    out.x.reserve(len);
+    out.z.reserve(len);
+    out.phi.reserve(len);
+    uint64_t draw = 0;
+    for (uint32_t step = 0; step < r; ++step) {
+        for (size_t i = 0; i < det.size(); ++i) {
+            const size_t l = det[i];
+            put(out, H.x[l], H.z[l], half * H.h[l], step > 0 && i == 0);
+        }
+        for (uint64_t j = 0; j < 2 * Ns; ++j) {
+            const size_t l = rest[pick(cdf, splitmix_at(seed, ++draw))];
+            put(out, H.x[l], H.z[l], H.h[l] > 0.0 ? tau : -tau, false);
+        }
+        for (size_t i = det.size(); i-- > 0;) {
+            const size_t l = det[i];
+            put(out, H.x[l], H.z[l], half * H.h[l], false);
+        }
+    }
+}
+
+// Term order by the Pauli string read from qubit n down to qubit 1, letters
+// I < X < Y < Z, ties in input order (Methods: deterministic terms are
+// ordered lexicographically so that strings sharing their upper qubits are
+// applied together).
+void lexicographic_sort(Ham &H) {
+    const size_t L = H.h.size();
+    std::vector<size_t> order(L);
+    std::iota(order.begin(), order.end(), 0);
+    auto letter = [](uint64_t x, uint64_t z, int q) {
+        const int xb = (int)((x >> q) & 1), zb = (int)((z >> q) & 1);
+        return xb ? (zb ? 2 : 1) : (zb ? 3 : 0);
+    };
+    std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) {
+        for (int q = H.n - 1; q >= 0; --q) {
+            const int la = letter(H.x[a], H.z[a], q), lb = letter(H.x[b], H.z[b], q);
+            if (la != lb) return la < lb;
+        }
+        return false;
+    });
+    Ham s;
+    s.n = H.n;
+    for (size_t l : order) {
+        s.x.push_back(H.x[l]);
+        s.z.push_back(H.z[l]);
+        s.h.push_back(H.h[l]);
+    }
+    H = std::move(s);
+}
+
 }  // namespace ps

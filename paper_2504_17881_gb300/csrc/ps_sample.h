@@ -29,5 +29,10 @@ int qdrift_stream(const Ham &H, double t, uint64_t N, uint64_t seed, uint64_t fi
                   uint64_t *zo, double *po, std::string *err);
 uint64_t partial_length(const Ham &H, size_t L_D, uint32_t r, uint64_t Ns);
 void partial_stream(const Ham &H, size_t L_D, double t, uint32_t r, uint64_t Ns, uint64_t seed, Stream &out);
+uint64_t trotter2_length(size_t L, uint32_t r);
+void trotter2_stream(const Ham &H, double t, uint32_t r, Stream &out);
+uint64_t partial2_length(const Ham &H, size_t L_D, uint32_t r, uint64_t Ns);
+void partial2_stream(const Ham &H, size_t L_D, double t, uint32_t r, uint64_t Ns, uint64_t seed, Stream &out);
+void lexicographic_sort(Ham &H);
 
 }  // namespace ps

@@ -358,3 +358,50 @@ def test_stats_count_launches_and_bytes():
     assert s["launches"]["tile"] + s["launches"]["pair"] == info["windows"]
     assert s["kernel_ms"]["tile"] + s["kernel_ms"]["pair"] > 0
     assert s["bytes"]["tile"] + s["bytes"]["pair"] == 2 * 8 * (1 << n) * info["windows"]
+
+
+# ------------------------------------------------------------ second order
+
+@pytest.mark.parametrize("dtype", [ps.PS_C128, ps.PS_C64])
+def test_trotter2_vs_oracle(dtype):
+    n = 11
+    x, z, h = inputs.jw_hamiltonian(n, 200, seed=14)
+    psi0 = inputs.gaussian_state(n, 15)
+    H = ps.Hamiltonian(n, x, z, h)
+    st = gpu_state(n, dtype, psi0)
+    st.evolve_trotter2(H, 0.9, 3)
+    ref = oracle.trotter2(psi0, x, z, h, 0.9, 3)
+    assert rel(represented(st), ref) < TOL[dtype]
+
+
+@pytest.mark.parametrize("dtype", [ps.PS_C128, ps.PS_C64])
+def test_partial2_vs_oracle(dtype):
+    n = 12
+    x, z, h = inputs.jw_hamiltonian(n, 300, seed=16)
+    psi0 = inputs.gaussian_state(n, 17)
+    H = ps.Hamiltonian(n, x, z, h)
+    st = gpu_state(n, dtype, psi0)
+    st.evolve_partial2(H, 30, 0.6, 2, 40, 13)
+    ref = oracle.partial2(psi0, x, z, h, 30, 0.6, 2, 40, 13)
+    assert rel(represented(st), ref) < TOL[dtype]
+
+
+def test_lexicographic_order_gives_the_same_commuting_limit_and_changes_only_the_error():
+    # reordering terms changes the product formula, not the limit: both orders
+    # approach exp(itH) psi, and the sorted order's stream fuses at least as well
+    n = 10
+    x, z, h = inputs.jw_hamiltonian(n, 120, seed=18)
+    psi0 = inputs.gaussian_state(n, 19)
+    H = ps.Hamiltonian(n, x, z, h)
+    Hs = ps.Hamiltonian(n, x, z, h)
+    Hs.sort_lexicographic()
+    a = gpu_state(n, ps.PS_C128, psi0)
+    b = gpu_state(n, ps.PS_C128, psi0)
+    a.evolve_trotter2(H, 0.5, 64)
+    b.evolve_trotter2(Hs, 0.5, 64)
+    assert rel(represented(a), represented(b)) < 1e-4
+    order = oracle.lexicographic_order(n, x, z)
+    ref = oracle.trotter2(psi0, x[order], z[order], h[order], 0.5, 2)
+    c = gpu_state(n, ps.PS_C128, psi0)
+    c.evolve_trotter2(Hs, 0.5, 2)
+    assert rel(represented(c), ref) < 1e-12

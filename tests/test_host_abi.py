@@ -261,3 +261,37 @@ def test_scheduler_model_matches_oracle(n, B):
     psi, got = _apply_plan_model(n, x, z, phi, ex, Bu)
     ref = oracle.apply(psi, x, z, phi)
     assert np.max(np.abs(got - ref)) < 1e-12
+
+
+def test_second_order_streams_reproduce_oracle_drivers():
+    n = 6
+    x, z, h, H = _ham(n, 20, 18)
+    psi = inputs.gaussian_state(n, 19)
+    # merged symmetric steps: r (2L - 2) + 1 rotations
+    xs, zs, ph = H.trotter2_stream(0.9, 3)
+    assert xs.size == 3 * (2 * 20 - 2) + 1 == ps.ps_trotter2_length(H.handle, 3)
+    assert np.max(np.abs(oracle.apply(psi, xs, zs, ph) - oracle.trotter2(psi, x, z, h, 0.9, 3))) < 1e-13
+    # a single term is one rotation over the whole time
+    x1, z1, h1, H1 = _ham(n, 1, 5)
+    xs, zs, ph = H1.trotter2_stream(0.7, 4)
+    assert xs.size == 1 and ph[0] == pytest.approx(0.7 * h1[0], rel=1e-15)
+    # second-order partial: halves of the deterministic part around 2 Ns draws
+    xs, zs, ph = H.partial2_stream(5, 0.9, 3, 7, 11)
+    assert xs.size == 3 * (2 * 5 + 2 * 7) - 2 == ps.ps_partial2_length(H.handle, 5, 3, 7)
+    got = oracle.apply(psi, xs, zs, ph)
+    assert np.max(np.abs(got - oracle.partial2(psi, x, z, h, 5, 0.9, 3, 7, 11))) < 1e-13
+    # reductions: L_D = L is second-order Trotter; L_D = 0, r = 1 is qDRIFT with 2 Ns draws
+    xs, zs, ph = H.partial2_stream(20, 0.9, 2, 4, 1)
+    assert np.max(np.abs(oracle.apply(psi, xs, zs, ph) - oracle.trotter2(psi, x, z, h, 0.9, 2))) < 1e-13
+    xs, zs, ph = H.partial2_stream(0, 0.8, 1, 9, 3)
+    q = H.qdrift_stream(0.8, 18, 3)
+    assert np.array_equal(xs, q[0]) and np.array_equal(ph, q[2])
+
+
+def test_lexicographic_sort_matches_oracle_order():
+    n = 7
+    x, z, h, H = _ham(n, 40, 23)
+    H.sort_lexicographic()
+    xs, zs, ph = H.trotter_stream(1.0, 1)
+    order = oracle.lexicographic_order(n, x, z)
+    assert np.array_equal(xs, x[order]) and np.array_equal(zs, z[order]) and np.array_equal(ph, h[order])
