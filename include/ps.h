@@ -288,6 +288,27 @@ int ps_partial2_stream(const ps_ham *ham, size_t L_D, double t, uint32_t r, uint
  * their upper qubits are applied together). */
 int ps_ham_sort_lexicographic(ps_ham *ham);
 
+/* Robust-phase-estimation signal (Methods, "Data analysis"):
+ *   Z_m = g(delta 2^m) = <psi0| U(delta)^(2^m) |psi0>,  m = 0..M,
+ * U(delta) one step of the order-1 or order-2 product formula (partially
+ * randomised when L_D < L and Ns > 0: Ns draws per step at first order,
+ * 2 Ns at second).  The state on `work` is continued from round to round,
+ * so 2^M steps are applied in total; the draws continue one seed's stream,
+ * so Z_m equals a single run of 2^m steps.  Z_out: 2 (M + 1) doubles.
+ * Synchronous. */
+int ps_rpe_signal(ps_state *work, const ps_state *psi0, const ps_ham *ham, int order, size_t L_D, double delta,
+                  uint32_t M, uint64_t Ns, uint64_t seed, double *Z_out);
+
+/* The deterministic size L_D that minimises the cost model of the
+ * partially randomised method (Methods, "Hamiltonian simulation"),
+ *   C_tot = a L_D / (eps delta) + b lambda_R^2 / eps^2,
+ * with the step delta = sqrt(eps / C) set by the analytic bound C(L_D) of
+ * ps_ham_trotter_bound (the paper uses a fitted C instead; Methods).
+ * L_D runs over 0..L (terms by decreasing |h|); ties keep the smaller L_D.
+ * delta_out is +inf when C = 0.  Host only, O(L^2). */
+int ps_partial_optimize_split(const ps_ham *ham, double eps, double a, double b, size_t *L_D_out, double *delta_out,
+                              double *cost_out);
+
 /* ------------------------------------------------------------ statistics */
 
 /* Counters since creation or the last reset; synchronises the stream when

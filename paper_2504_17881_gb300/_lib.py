@@ -128,6 +128,8 @@ _SIGS = {
     "ps_partial2_length": (_u64, [_vp, _sz, _u32, _u64]),
     "ps_partial2_stream": (_i, [_vp, _sz, _d, _u32, _u64, _u64, _vp, _vp, _vp]),
     "ps_ham_sort_lexicographic": (_i, [_vp]),
+    "ps_rpe_signal": (_i, [_vp, _vp, _vp, _i, _sz, _d, _u32, _u64, _u64, _vp]),
+    "ps_partial_optimize_split": (_i, [_vp, _d, _d, _d, ctypes.POINTER(_sz), ctypes.POINTER(_d), ctypes.POINTER(_d)]),
     "ps_ham_trotter_bound": (_i, [_vp, _sz, ctypes.POINTER(_d)]),
     "ps_ham_features": (_i, [_vp, _vp, _vp, _sz, _d, _u32, _vp]),
     "ps_ham_error_coefficient": (_i, [_vp, _vp, _vp, _sz, _vp]),
@@ -650,3 +652,22 @@ def ps_partial2_stream(ham: int, L_D: int, t: float, r: int, Ns: int, seed: int)
 
 def ps_ham_sort_lexicographic(ham: int):
     _check(lib.ps_ham_sort_lexicographic(ctypes.c_void_p(ham)))
+
+
+def ps_rpe_signal(work: int, psi0: int, ham: int, order: int, L_D: int, delta: float, M: int, Ns: int = 0,
+                  seed: int = 0) -> np.ndarray:
+    """Z_m, m = 0..M, as a complex128 array."""
+    out = np.zeros(2 * (M + 1), dtype=np.float64)
+    _check(lib.ps_rpe_signal(ctypes.c_void_p(work), ctypes.c_void_p(psi0), ctypes.c_void_p(ham), order, L_D, delta,
+                             M, Ns, seed, _ptr(out)))
+    return out[0::2] + 1j * out[1::2]
+
+
+def ps_partial_optimize_split(ham: int, eps: float, a: float, b: float):
+    """(L_D, delta, cost) minimising the partially randomised cost model."""
+    L_D = _sz()
+    d = _d()
+    c = _d()
+    _check(lib.ps_partial_optimize_split(ctypes.c_void_p(ham), eps, a, b, ctypes.byref(L_D), ctypes.byref(d),
+                                         ctypes.byref(c)))
+    return int(L_D.value), d.value, c.value

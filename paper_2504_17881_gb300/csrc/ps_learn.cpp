@@ -284,6 +284,73 @@ int ps_trotter_stream(const ps_ham *ham, double t, uint32_t r, uint64_t *x_out, 
     return PS_OK;
 }
 
+int ps_rpe_signal(ps_state *work, const ps_state *psi0, const ps_ham *ham, int order, size_t L_D, double delta,
+                  uint32_t M, uint64_t Ns, uint64_t seed, double *Z_out) {
+    if (!work || !psi0 || !ham || !Z_out) return lfail(PS_ERR_ARG, "null argument");
+    if (order != 1 && order != 2) return lfail(PS_ERR_ARG, "order must be 1 or 2");
+    if (L_D > ham->H.h.size()) return lfail(PS_ERR_ARG, "L_D exceeds the number of terms");
+    if (M > 30) return lfail(PS_ERR_ARG, "M must be at most 30");
+    if (!std::isfinite(delta)) return lfail(PS_ERR_ARG, "non-finite step size");
+    if (int rc = ps_copy_state(work, psi0)) return rc;
+    // Z_m = <psi|U(delta)^(2^m)|psi>: the state is continued from 2^(m-1) to
+    // 2^m steps, so all rounds together apply 2^M steps
+    uint64_t done = 0;
+    for (uint32_t m = 0; m <= M; ++m) {
+        const uint64_t target = 1ull << m;
+        Stream s;
+        product_steps(ham->H, order, L_D, delta, Ns, seed, done, target - done, s);
+        if (int rc = ps_apply_rotations(work, s.x.data(), s.z.data(), s.phi.data(), s.size())) return rc;
+        done = target;
+        if (int rc = ps_overlap(psi0, work, Z_out + 2 * m)) return rc;
+    }
+    return PS_OK;
+}
+
+int ps_partial_optimize_split(const ps_ham *ham, double eps, double a, double b, size_t *L_D_out, double *delta_out,
+                              double *cost_out) {
+    if (!ham || !L_D_out) return lfail(PS_ERR_ARG, "null argument");
+    if (!(eps > 0.0) || !(a >= 0.0) || !(b >= 0.0)) return lfail(PS_ERR_ARG, "eps must be positive, a and b >= 0");
+    const Ham &H = ham->H;
+    std::vector<size_t> order(H.h.size());
+    for (size_t i = 0; i < order.size(); ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](size_t p, size_t q) { return std::fabs(H.h[p]) > std::fabs(H.h[q]); });
+    double lam = 0.0;
+    for (double v : H.h) lam += std::fabs(v);
+    // S(L_D) = sum over ordered pairs (l, k) in D that anticommute of |h_l| |h_k|,
+    // grown one term at a time
+    double S = 0.0, lam_d = 0.0;
+    double best = 0.0, best_delta = 0.0;
+    size_t best_L = 0;
+    for (size_t LD = 0; LD <= order.size(); ++LD) {
+        if (LD > 0) {
+            const size_t j = order[LD - 1];
+            double acc = 0.0;
+            for (size_t i = 0; i + 1 < LD; ++i) {
+                const size_t k = order[i];
+                if (anticommute(H.x[j], H.z[j], H.x[k], H.z[k])) acc += std::fabs(H.h[k]);
+            }
+            S += 2.0 * std::fabs(H.h[j]) * acc;
+            lam_d += std::fabs(H.h[j]);
+        }
+        const double lam_r = std::max(0.0, lam - lam_d);
+        const double C = 4.0 * S + lam_r * lam_d * lam_d + lam_d * lam_r * lam_r;
+        // C delta^2 <= eps fixes the largest step; C = 0 leaves the step free
+        const double delta = C > 0.0 ? std::sqrt(eps / C) : INFINITY;
+        const double cost_d = (LD == 0 || !std::isfinite(delta)) ? 0.0 : a * (double)LD / (eps * delta);
+        const double cost = cost_d + b * lam_r * lam_r / (eps * eps);
+        if (LD == 0 || cost < best) {
+            best = cost;
+            best_L = LD;
+            best_delta = delta;
+        }
+    }
+    *L_D_out = best_L;
+    if (delta_out) *delta_out = best_delta;
+    if (cost_out) *cost_out = best;
+    return PS_OK;
+}
+
 int ps_trotter_sweep(ps_state *work, const ps_state *psi0, const ps_ham *ham, double t, double eps, uint32_t r_max,
                      uint32_t *r_out, uint64_t *rotations_out, double *g_out) {
     if (!work || !psi0 || !ham || !r_out) return lfail(PS_ERR_ARG, "null argument");

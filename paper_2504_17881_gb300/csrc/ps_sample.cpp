@@ -238,6 +238,44 @@ void partial2_stream(const Ham &H, size_t L_D, double t, uint32_t r, uint64_t Ns
     }
 }
 
+// Steps [step0, step0 + nsteps) of a product formula with step size delta
+// (first or second order; partially randomised when H_R is sampled), exactly
+// the factors those steps have inside a run of any longer length: step s
+// draws samples s * draws_per_step + 1, ... of the seed's stream.  Second-
+// order factors are merged within the chunk, never across its ends.
+void product_steps(const Ham &H, int order, size_t L_D, double delta, uint64_t Ns, uint64_t seed, uint64_t step0,
+                   uint64_t nsteps, Stream &out) {
+    std::vector<size_t> det, rest;
+    split_terms(H, L_D, det, rest);
+    std::vector<double> cdf = running_abs(H.h, rest);
+    const double lam_r = rest.empty() ? 0.0 : cdf.back();
+    const bool sample = !rest.empty() && Ns > 0 && lam_r > 0.0;
+    const uint64_t per = sample ? (order == 2 ? 2 * Ns : Ns) : 0;
+    const double tau = sample ? lam_r * delta / (double)per : 0.0;
+    const double half = 0.5 * delta;
+    out = Stream();
+    uint64_t draw = step0 * per;
+    for (uint64_t s = 0; s < nsteps; ++s) {
+        if (order == 1) {
+            for (size_t l : det) put(out, H.x[l], H.z[l], delta * H.h[l], false);
+        } else {
+            for (size_t i = 0; i < det.size(); ++i) {
+                const size_t l = det[i];
+                put(out, H.x[l], H.z[l], half * H.h[l], s > 0 && i == 0);
+            }
+        }
+        for (uint64_t j = 0; j < per; ++j) {
+            const size_t l = rest[pick(cdf, splitmix_at(seed, ++draw))];
+            put(out, H.x[l], H.z[l], H.h[l] > 0.0 ? tau : -tau, false);
+        }
+        if (order == 2)
+            for (size_t i = det.size(); i-- > 0;) {
+                const size_t l = det[i];
+                put(out, H.x[l], H.z[l], half * H.h[l], !sample && i == det.size() - 1);
+            }
+    }
+}
+
 // Term order by the Pauli string read from qubit n down to qubit 1, letters
 // I < X < Y < Z, ties in input order (Methods: deterministic terms are
 // ordered lexicographically so that strings sharing their upper qubits are

@@ -405,3 +405,25 @@ def test_lexicographic_order_gives_the_same_commuting_limit_and_changes_only_the
     c = gpu_state(n, ps.PS_C128, psi0)
     c.evolve_trotter2(Hs, 0.5, 2)
     assert rel(represented(c), ref) < 1e-12
+
+
+@pytest.mark.parametrize("order,L_D,Ns", [(1, 40, 0), (2, 40, 0), (1, 6, 5), (2, 6, 3)])
+def test_rpe_signal_reuses_state_and_matches_separate_runs(order, L_D, Ns):
+    # Z_m = g(delta 2^m) from one continued state equals 2^m steps run from psi0
+    n = 9
+    x, z, h = inputs.jw_hamiltonian(n, 40, seed=28)
+    psi0 = inputs.gaussian_state(n, 29)
+    H = ps.Hamiltonian(n, x, z, h)
+    p0 = gpu_state(n, ps.PS_C128, psi0)
+    work = gpu_state(n, ps.PS_C128, psi0)
+    delta, M, seed = 0.07, 5, 31
+    Z = ps.ps_rpe_signal(work.handle, p0.handle, H.handle, order, L_D, delta, M, Ns, seed)
+    for m in range(M + 1):
+        steps = 1 << m
+        t = delta * steps
+        if order == 1:
+            ref = oracle.partial(psi0, x, z, h, L_D, t, steps, Ns, seed)
+        else:
+            ref = oracle.partial2(psi0, x, z, h, L_D, t, steps, Ns, seed)
+        g = np.vdot(psi0, ref)
+        assert abs(Z[m] - g) < 1e-12, (m, Z[m], g)

@@ -10,6 +10,7 @@
   tile in tile coordinates (a numpy model of the kernel's index algebra).
 """
 import ctypes
+import math
 import os
 import re
 
@@ -295,3 +296,26 @@ def test_lexicographic_sort_matches_oracle_order():
     xs, zs, ph = H.trotter_stream(1.0, 1)
     order = oracle.lexicographic_order(n, x, z)
     assert np.array_equal(xs, x[order]) and np.array_equal(zs, z[order]) and np.array_equal(ph, h[order])
+
+
+def test_split_optimizer_matches_enumeration_with_the_oracle_bound():
+    from oracle import learned as OL
+    n = 6
+    x, z, h, H = _ham(n, 18, 27)
+    lam = float(np.abs(h).sum())
+    order = OL.split_order(h)
+    for eps, a, b in ((1e-3, 1.0, 1.0), (1e-2, 5.0, 0.1), (1e-3, 0.01, 10.0)):
+        costs = []
+        for L_D in range(0, len(h) + 1):
+            C = OL.trotter_bound(n, x, z, h, L_D)
+            lam_r = sum(abs(float(h[k])) for k in order[L_D:])
+            delta = math.sqrt(eps / C) if C > 0 else math.inf
+            cd = 0.0 if (L_D == 0 or math.isinf(delta)) else a * L_D / (eps * delta)
+            costs.append(cd + b * lam_r ** 2 / eps ** 2)
+        want = int(np.argmin(costs))
+        L_D, delta, cost = ps.ps_partial_optimize_split(H.handle, eps, a, b)
+        assert L_D == want and cost == pytest.approx(costs[want], rel=1e-12)
+    # all-randomised when the deterministic part is expensive, all-deterministic when sampling is
+    assert ps.ps_partial_optimize_split(H.handle, 1e-3, 1e6, 1e-6)[0] == 0
+    assert ps.ps_partial_optimize_split(H.handle, 1e-3, 1e-6, 1e6)[0] == len(h)
+    assert lam > 0
