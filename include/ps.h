@@ -309,6 +309,27 @@ int ps_rpe_signal(ps_state *work, const ps_state *psi0, const ps_ham *ham, int o
 int ps_partial_optimize_split(const ps_ham *ham, double eps, double a, double b, size_t *L_D_out, double *delta_out,
                               double *cost_out);
 
+/* ----------------------------------------------------- sharded schedule
+ *
+ * A state of n qubits spread over 2^m ranks by its upper m qubits (rank rho
+ * holds amplitudes k with k >> (n - m) = rho), as the paper distributes it
+ * over nodes (Results, Eq. 1).  ps_shard_plan splits a rotation sequence
+ * into windows for rank `rank`: a window is a maximal run of rotations whose
+ * X masks have one common nonzero part X above bit n - m (or none).  For a
+ * window with X, the rank exchanges its slab with rank rho ^ X once (one
+ * point-to-point send and receive of 2^(n-m) amplitudes) and applies the
+ * window's rotations to the two slabs as one state of n - m + 1 qubits: its
+ * own slab as the half with local top bit 0, the partner's as the half with
+ * bit 1.  It keeps its own half; the partner does the same with the roles
+ * swapped.  A window without X is applied to the slab alone (n - m qubits).
+ * Outputs, for window w: partner[w] (-1: local), win_end[w] (one past its
+ * last rotation); for every rotation: its local masks and angle (the upper
+ * Z bits become a sign of the angle or the local top Z bit; see
+ * csrc/ps_shard.cpp).  Arrays sized `count` (windows <= rotations). */
+int ps_shard_plan(int n, int m, int rank, const uint64_t *x, const uint64_t *z, const double *phi, size_t count,
+                  size_t *n_windows, int32_t *partner, uint64_t *win_end, uint64_t *x_out, uint64_t *z_out,
+                  double *phi_out);
+
 /* ------------------------------------------------------------ statistics */
 
 /* Counters since creation or the last reset; synchronises the stream when

@@ -129,6 +129,7 @@ _SIGS = {
     "ps_partial2_stream": (_i, [_vp, _sz, _d, _u32, _u64, _u64, _vp, _vp, _vp]),
     "ps_ham_sort_lexicographic": (_i, [_vp]),
     "ps_rpe_signal": (_i, [_vp, _vp, _vp, _i, _sz, _d, _u32, _u64, _u64, _vp]),
+    "ps_shard_plan": (_i, [_i, _i, _i, _vp, _vp, _vp, _sz, ctypes.POINTER(_sz), _vp, _vp, _vp, _vp, _vp]),
     "ps_partial_optimize_split": (_i, [_vp, _d, _d, _d, ctypes.POINTER(_sz), ctypes.POINTER(_d), ctypes.POINTER(_d)]),
     "ps_ham_trotter_bound": (_i, [_vp, _sz, ctypes.POINTER(_d)]),
     "ps_ham_features": (_i, [_vp, _vp, _vp, _sz, _d, _u32, _vp]),
@@ -671,3 +672,24 @@ def ps_partial_optimize_split(ham: int, eps: float, a: float, b: float):
     _check(lib.ps_partial_optimize_split(ctypes.c_void_p(ham), eps, a, b, ctypes.byref(L_D), ctypes.byref(d),
                                          ctypes.byref(c)))
     return int(L_D.value), d.value, c.value
+
+
+def ps_shard_plan(n: int, m: int, rank: int, x, z, phi):
+    """Windows of a rotation sequence for one rank of 2^m: a list of
+    (partner or -1, local x, local z, local phi)."""
+    x, z, phi = _u64a(x), _u64a(z), _f64a(phi)
+    cnt = len(phi)
+    nw = _sz()
+    partner = np.zeros(max(cnt, 1), dtype=np.int32)
+    end = np.zeros(max(cnt, 1), dtype=np.uint64)
+    xo = np.zeros(max(cnt, 1), dtype=np.uint64)
+    zo = np.zeros(max(cnt, 1), dtype=np.uint64)
+    po = np.zeros(max(cnt, 1), dtype=np.float64)
+    _check(lib.ps_shard_plan(n, m, rank, _ptr(x), _ptr(z), _ptr(phi), cnt, ctypes.byref(nw), _ptr(partner), _ptr(end),
+                             _ptr(xo), _ptr(zo), _ptr(po)))
+    out, start = [], 0
+    for w in range(nw.value):
+        e = int(end[w])
+        out.append((int(partner[w]), xo[start:e].copy(), zo[start:e].copy(), po[start:e].copy()))
+        start = e
+    return out
