@@ -341,9 +341,14 @@ __device__ __forceinline__ void tile_pass(const typename CT<R>::T *src, typename
         // Coset representatives: zero bits inserted at the round's pivots.  The
         // insertion is linear over XOR and q = tid | (group << lgT) splits into
         // disjoint fields, so j0 = spread(tid) ^ spread(group << lgT).
+        // the bits below each pivot, once per round: inserting a zero at pivot
+        // p maps q to ((q & ~m) << 1) | (q & m), m = 2^p - 1
+        uint32_t pmask[G];
+#pragma unroll
+        for (int i = 0; i < G; ++i) pmask[i] = (1u << piv[i]) - 1u;
         auto spread = [&](uint32_t q) {
 #pragma unroll
-            for (int i = 0; i < G; ++i) q = ((q >> piv[i]) << (piv[i] + 1)) | (q & ((1u << piv[i]) - 1));
+            for (int i = 0; i < G; ++i) q = ((q & ~pmask[i]) << 1) | (q & pmask[i]);
             return q;
         };
         const uint32_t j_tid = spread((uint32_t)tid);
