@@ -260,16 +260,33 @@ __device__ __forceinline__ void tile_pass(const typename CT<R>::T *src, typename
         // Gray steps 1, 2, 1 of every group of four iterations use v[it_shift]
         // and v[it_shift + 1] from registers; only the fourth reads the window
         const uint64_t va = niter > 1 ? P.v[it_shift] : 0, vb = niter > 2 ? P.v[it_shift + 1] : 0;
-        uint64_t vi = 0;
-        for (int i = 0; i < niter; ++i) {
-            if (i & 1)
-                vi ^= va;
-            else if (i & 2)
-                vi ^= vb;
-            else if (i)
-                vi ^= P.v[it_shift + (__ffs(i) - 1)];
-            const int gi = i ^ (i >> 1);
-            cp_async16(smem + (size_t)(tid + (gi << lgB)) * 16, gbase + ((base ^ vi) << LS) + off);
+        if (n <= 32) {
+            // amplitude indices fit 32 bits: one XOR and one wide multiply-add per chunk
+            const char *gb = gbase + off;
+            const uint32_t b32 = (uint32_t)base, va32 = (uint32_t)va, vb32 = (uint32_t)vb;
+            uint32_t vi = 0;
+            for (int i = 0; i < niter; ++i) {
+                if (i & 1)
+                    vi ^= va32;
+                else if (i & 2)
+                    vi ^= vb32;
+                else if (i)
+                    vi ^= (uint32_t)P.v[it_shift + (__ffs(i) - 1)];
+                const int gi = i ^ (i >> 1);
+                cp_async16(smem + (size_t)(tid + (gi << lgB)) * 16, gb + (uint64_t)(b32 ^ vi) * (1u << LS));
+            }
+        } else {
+            uint64_t vi = 0;
+            for (int i = 0; i < niter; ++i) {
+                if (i & 1)
+                    vi ^= va;
+                else if (i & 2)
+                    vi ^= vb;
+                else if (i)
+                    vi ^= P.v[it_shift + (__ffs(i) - 1)];
+                const int gi = i ^ (i >> 1);
+                cp_async16(smem + (size_t)(tid + (gi << lgB)) * 16, gbase + ((base ^ vi) << LS) + off);
+            }
         }
     } else {
         for (uint32_t ch = (uint32_t)tid; ch < (1u << lgchunks); ch += blockDim.x)
