@@ -287,6 +287,12 @@ int ps_partial2_stream(const ps_ham *ham, size_t L_D, double t, uint32_t r, uint
  * deterministic terms are ordered lexicographically, so strings that share
  * their upper qubits are applied together). */
 int ps_ham_sort_lexicographic(ps_ham *ham);
+/* The randomised part's samples per Trotter stage exactly as printed
+ * (Methods, "Data analysis"): kappa = delta / (0.2 pi),
+ * r = ceil(kappa lambda_R^2 delta^2 2^M).  The printed form grows like
+ * delta^3 and looks garbled, so the drivers never use it; callers pass
+ * their own sample count.  0 for negative arguments or M outside 0..62. */
+uint64_t ps_partial_sample_count(double delta, double lambda_R, int M);
 
 /* Robust-phase-estimation signal (Methods, "Data analysis"):
  *   Z_m = g(delta 2^m) = <psi0| U(delta)^(2^m) |psi0>,  m = 0..M,

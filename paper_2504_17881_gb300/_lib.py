@@ -128,6 +128,7 @@ _SIGS = {
     "ps_partial2_length": (_u64, [_vp, _sz, _u32, _u64]),
     "ps_partial2_stream": (_i, [_vp, _sz, _d, _u32, _u64, _u64, _vp, _vp, _vp]),
     "ps_ham_sort_lexicographic": (_i, [_vp]),
+    "ps_partial_sample_count": (_u64, [_d, _d, _i]),
     "ps_rpe_signal": (_i, [_vp, _vp, _vp, _i, _sz, _d, _u32, _u64, _u64, _vp]),
     "ps_shard_plan": (_i, [_i, _i, _i, _vp, _vp, _vp, _sz, ctypes.POINTER(_sz), _vp, _vp, _vp, _vp, _vp]),
     "ps_partial_optimize_split": (_i, [_vp, _d, _d, _d, ctypes.POINTER(_sz), ctypes.POINTER(_d), ctypes.POINTER(_d)]),
@@ -693,3 +694,8 @@ def ps_shard_plan(n: int, m: int, rank: int, x, z, phi):
         out.append((int(partner[w]), xo[start:e].copy(), zo[start:e].copy(), po[start:e].copy()))
         start = e
     return out
+
+
+def ps_partial_sample_count(delta: float, lambda_R: float, M: int) -> int:
+    """The randomised part's samples per stage as the paper prints it (opt-in; looks garbled)."""
+    return int(lib.ps_partial_sample_count(delta, lambda_R, M))

@@ -672,6 +672,11 @@ int ps_partial2_stream(const ps_ham *ham, size_t L_D, double t, uint32_t r, uint
     return PS_OK;
 }
 
+uint64_t ps_partial_sample_count(double delta, double lambda_R, int M) {
+    if (!(delta >= 0.0) || !(lambda_R >= 0.0) || M < 0 || M > 62) return 0;
+    return printed_sample_count(delta, lambda_R, M);
+}
+
 int ps_ham_sort_lexicographic(ps_ham *ham) {
     if (!ham) return fail(PS_ERR_ARG, "null Hamiltonian");
     lexicographic_sort(ham->H);
