@@ -286,7 +286,7 @@ def run_ours(args):
     bytes_per_launch = 2.0 * 8.0 * (1 << N_QUBITS)
     achieved = bytes_per_launch / (tile_ms / tile_n / 1e3) / 1e9 if tile_ms > 0 else None
     peak, peak_kind = hbm_peak()
-    roofline = {"bound": "hbm", "kernel": "k_tile<float,3,2>", "achieved": achieved, "peak": peak, "unit": "GB/s",
+    roofline = {"bound": "hbm", "kernel": "k_tile<float,3,4>", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": (achieved / peak) if achieved else None, "traffic": kernel_traffic(),
                 "peak_source": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
                 else "fallback 6.8 TB/s", "algorithmic_bytes_per_launch": bytes_per_launch,

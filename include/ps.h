@@ -69,6 +69,17 @@ typedef struct ps_tuning {
     int kernel_timing; /* 1: time every launch with CUDA events (read with ps_get_stats) */
     int reg_groups;    /* register groups of 2^G amplitudes per thread: 1, 2 or 4 (default 2;
                           capped at 32 complex64 / 16 complex128 amplitudes per thread) */
+    int seg_bits;      /* c_min: log2 of the fewest contiguous amplitudes per segment of a
+                          tile, 1..B (default 4 for PS_C64, 3 for PS_C128: 128-byte
+                          segments).  A smaller value leaves more tile bits for the window
+                          span, so more rotations share a pass, at a finer DRAM access
+                          granularity (2^c_min * 8 or 16 bytes). */
+    int tile_threads;  /* most threads per CTA of the tile kernel: 64, 128, 256 or 512 (0 =
+                          default: 256 while a thread's register groups hold at most 16
+                          complex64 / 8 complex128 amplitudes, else 128; a request above that
+                          default is capped to it).  Fewer threads give each thread more
+                          register batches per round, spreading its fixed per-round work over
+                          more amplitudes. */
 } ps_tuning;
 
 /* Counters of a state handle since creation or the last ps_reset_stats. */

@@ -29,7 +29,8 @@ class PsError(RuntimeError):
 
 class ps_tuning(ctypes.Structure):
     _fields_ = [("tile_bits", ctypes.c_int), ("group_bits", ctypes.c_int), ("max_window", ctypes.c_int),
-                ("pair_single", ctypes.c_int), ("kernel_timing", ctypes.c_int), ("reg_groups", ctypes.c_int)]
+                ("pair_single", ctypes.c_int), ("kernel_timing", ctypes.c_int), ("reg_groups", ctypes.c_int),
+                ("seg_bits", ctypes.c_int), ("tile_threads", ctypes.c_int)]
 
 
 class ps_stats(ctypes.Structure):

@@ -210,7 +210,7 @@ int launch_plan(ps_state *st, const Plan &p) {
             e = launch_pair(st->dtype, st->psi, st->n, pp, kdelta, st->stream, st->num_sms);
         } else {
             fill_tile_params(p, w, tp);
-            e = launch_tile(st->dtype, p.G, p.NG, st->psi, st->n, tp, kdelta, st->stream);
+            e = launch_tile(st->dtype, p.G, p.NG, st->psi, st->n, tp, kdelta, st->stream, p.threads);
         }
         if (e != 0) return cuda_fail((cudaError_t)e, w.kind == 1 ? "pair kernel launch" : "tile kernel launch");
         if (timing) {
@@ -282,7 +282,7 @@ extern "C" {
 
 const char *ps_last_error(void) { return g_err.c_str(); }
 
-int ps_abi_version(void) { return 1; }
+int ps_abi_version(void) { return 2; }
 
 int ps_device_count(void) {
     int n = 0;

@@ -71,6 +71,7 @@ struct Plan {
     int B = 0;  // tile bits used
     int G = 0;  // group bits used
     int NG = 0; // register groups per thread requested (0 = automatic)
+    int threads = 0;   // threads per tile-kernel CTA (0: the kernel's default)
     std::vector<WinDesc> win;
     std::vector<SubDesc> sub;
     std::vector<RotDesc> rot;
@@ -78,7 +79,7 @@ struct Plan {
 };
 
 struct Tuning {
-    int B, G, max_window, pair_single, kernel_timing, reg_groups;
+    int B, G, max_window, pair_single, kernel_timing, reg_groups, seg_bits, tile_threads;
 };
 
 Tuning resolve_tuning(const ps_tuning *t, int dtype);
@@ -237,7 +238,7 @@ void fill_tile_params(const Plan &p, const WinDesc &w, TileParams &tp);
 // After its rotations a pass applies a <- a + kdelta * a to every amplitude:
 // the part of the accumulated cos(phi) factors the state stores.
 int launch_tile(int dtype, int G, int ng_request, void *psi, int n, const TileParams &tp, double kdelta,
-                void *stream);
+                void *stream, int threads);
 int launch_pair(int dtype, void *psi, int n, const PairParams &pp, double kdelta, void *stream, int num_sms);
 int launch_reduce(int dtype, int what, const void *a, const void *b, int n, double *partials, double *out_dev,
                   void *stream);

@@ -200,7 +200,9 @@ Tuning resolve_tuning(const ps_tuning *t, int dtype) {
     r.max_window = (t && t->max_window) ? t->max_window : 64;
     r.pair_single = (t && t->pair_single) ? t->pair_single : 1;
     r.kernel_timing = t ? t->kernel_timing : 0;
-    r.reg_groups = (t && t->reg_groups) ? t->reg_groups : 2;
+    r.reg_groups = (t && t->reg_groups) ? t->reg_groups : (dtype == PS_C64 ? 4 : 2);
+    r.seg_bits = (t && t->seg_bits) ? t->seg_bits : (dtype == PS_C64 ? 4 : 3);
+    r.tile_threads = t ? t->tile_threads : 0;
     return r;
 }
 
@@ -220,6 +222,10 @@ int build_plan(int n, int dtype, const uint64_t *x, const uint64_t *z, const dou
     if (tun.pair_single != 1 && tun.pair_single != 2) return fail("pair_single must be 0, 1 or 2");
     if (tun.reg_groups != 0 && tun.reg_groups != 1 && tun.reg_groups != 2 && tun.reg_groups != 4)
         return fail("reg_groups must be 0, 1, 2 or 4");
+    if (tun.seg_bits < 1 || tun.seg_bits > tun.B) return fail("seg_bits must be in [1, tile_bits]");
+    if (tun.tile_threads != 0 && tun.tile_threads != 64 && tun.tile_threads != 128 && tun.tile_threads != 256 &&
+        tun.tile_threads != 512)
+        return fail("tile_threads must be 0, 64, 128, 256 or 512");
     if (count && (!x || !z || !phi)) return fail("null rotation array");
     for (size_t j = 0; j < count; ++j) {
         if ((x[j] | z[j]) >> n) {
@@ -236,14 +242,15 @@ int build_plan(int n, int dtype, const uint64_t *x, const uint64_t *z, const dou
     const int B = std::min(tun.B, n);
     if (n - B > 30) return fail("n - tile_bits must be <= 30");
     const int G = std::min(tun.G, B);
-    // a segment of at least 128 bytes keeps every DRAM access line-sized
-    const int cmin = std::min(dtype == PS_C64 ? 4 : 3, B);
+    // c_min: by default a segment of at least 128 bytes, so every DRAM access is line-sized
+    const int cmin = std::min(tun.seg_bits, B);
     p = Plan();
     p.n = n;
     p.dtype = dtype;
     p.B = B;
     p.G = G;
     p.NG = tun.reg_groups;
+    p.threads = tun.tile_threads;
     p.rotations = count;
     p.rot.resize(count);
     for (size_t j = 0; j < count; ++j) fill_coeffs(p.rot[j], x[j], z[j], phi[j]);

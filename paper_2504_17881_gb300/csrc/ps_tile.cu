@@ -4,9 +4,9 @@
 namespace ps {
 
 template <typename R, int G, int NG>
-__global__ void __launch_bounds__(kTileThreads, tile_min_blocks<R, G, NG>()) k_tile(typename CT<R>::T *__restrict__ psi,
-                                                          const __grid_constant__ TileParams P, int n, R kdelta) {
-    tile_pass<R, G, NG, false>(psi, psi, P, blockIdx.x, n, kdelta, true, true);
+__global__ void __launch_bounds__(tile_max_threads(sizeof(R), G, NG), 3) k_tile(typename CT<R>::T *__restrict__ psi,
+                                                                  const __grid_constant__ TileParams P, int n, R kdelta) {
+    tile_pass<R, G, NG, false, true>(psi, psi, P, blockIdx.x, n, kdelta, true, true);
 }
 
 // ------------------------------------------------------------------ launch
@@ -90,13 +90,15 @@ static cudaError_t launch_tile_g(int NG, unsigned grid, int threads, size_t byte
 }
 
 int launch_tile(int dtype, int G, int ng_request, void *psi, int n, const TileParams &tp, double kdelta,
-                void *stream) {
+                void *stream, int threads_request) {
     const int B = tp.c + tp.d;
     const size_t bytes = ((size_t)(dtype == PS_C64 ? 8 : 16) << B) + (size_t)tp.nrot * rec_bytes(dtype);
     const unsigned grid = 1u << (n - B);
     const int NG = groups_per_thread(dtype, G, B, ng_request);
     int threads = (1 << (B - G)) / NG;
-    if (threads > kTileThreads) threads = kTileThreads;
+    const int tmax = tile_max_threads(dtype == PS_C64 ? 4 : 8, G, NG);
+    const int cap = (threads_request > 0 && threads_request < tmax) ? threads_request : tmax;
+    if (threads > cap) threads = cap;
     cudaStream_t st = (cudaStream_t)stream;
     cudaError_t e;
     if (dtype == PS_C64) {

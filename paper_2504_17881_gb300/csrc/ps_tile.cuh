@@ -175,84 +175,68 @@ __device__ __forceinline__ uint64_t v_of(const TileParams &P, uint32_t x) {
     return acc;
 }
 
-// Fused window.  CTA blockIdx.x owns the coset T(k0) of 2^B = 2^(c+d)
-// amplitudes: tile index t = seg * 2^c + o <-> global index
+// Fused window.  A CTA owns the coset T(k0) of 2^B = 2^(c+d) amplitudes:
+// tile index t = seg * 2^c + o <-> global index
 //   idx(t) = k0 ^ V(t >> c) ^ (t & (2^c - 1)),
 // V(seg) = XOR of v[i] over the set bits i of seg (a linear map), and k0 =
-// blockIdx.x with zero bits inserted at the low c positions and at the
-// pivots of v.  The window arrives by value (P), so the CTA first issues the
-// 16-byte asynchronous copies of its whole tile into shared memory, then
+// the tile number H with zero bits inserted at the low c positions and at
+// the pivots of v.  The window arrives by value (P), so the CTA first issues
+// the 16-byte asynchronous copies of its whole tile into shared memory, then
 // builds its per-rotation tables while they are in flight.  Register rounds
-// follow: each thread owns NG groups of 2^G amplitudes {j0 ^ U(m)} and applies
-// the round's rotations to all of them; rounds exchange the tile through
-// shared memory, and the last round multiplies by 1 + kdelta and stores
-// straight to HBM, using idx(j0 ^ U(m)) = idx(j0) ^ W(m), W(m) = XOR of
-// W_i = V(u_i >> c) ^ (u_i & (2^c - 1)) over the bits i of m.  Group members
-// are visited in Gray-code order m = i ^ (i >> 1), one XOR per address.
-// Resident CTAs per SM the register budget is sized for: three when a thread
-// holds at most 16 complex64 (8 complex128) amplitudes, else two.
+// follow: each thread owns NG groups of 2^G amplitudes {j0 ^ U(m)} and
+// applies the round's rotations to all of them; rounds exchange the tile
+// through shared memory, and the last round multiplies by 1 + kdelta and
+// stores straight to HBM, using idx(j0 ^ U(m)) = idx(j0) ^ W(m), W(m) = XOR
+// of W_i = V(u_i >> c) ^ (u_i & (2^c - 1)) over the bits i of m.  Group
+// members are visited in Gray-code order m = i ^ (i >> 1), one XOR per
+// address.
+// Threads per CTA of the one-tile kernel: 256 while a batch of register
+// groups holds at most 16 complex64 (8 complex128) amplitudes, else 128, so
+// that three CTAs per SM (the shared-memory limit of 64 KB tiles) leave a
+// thread up to 80 or 168 registers.  Fewer threads with more amplitudes each
+// spread a thread's fixed work per round (descriptor decoding, coset
+// representatives, address bases) over more amplitudes.
+constexpr int tile_max_threads(int real_bytes, int G, int NG) { return (NG << G) * real_bytes <= 64 ? 256 : 128; }
+// Resident CTAs per SM the batched kernel's register budget is sized for:
+// three when a thread holds at most 16 complex64 (8 complex128) amplitudes,
+// else two.
 template <typename R, int G, int NG>
 constexpr int tile_min_blocks() {
     return (NG << G) * (int)sizeof(R) <= 64 ? 3 : 2;
 }
 
-// Per-pass tables of a CTA, one copy for every instance of the pass:
+// Per-window tables of a CTA, one copy for every instance of the pass:
 // V over each 4-bit nibble of a segment index, and the global offsets W_i of
-// the current round's group basis.
+// every round's group basis.
 static __shared__ uint64_t g_pass_nib[4][16];
 static __shared__ uint64_t g_pass_sub_w[kParamSub][kMaxG];
 
-// One tile pass: coset H of the window P (n-qubit state), read from src and
-// written to dst (the same buffer for an in-place pass).  Used by k_tile (one
-// tile per CTA) and by the batched kernel (many tiles per CTA); the leading
-// barrier keeps a CTA's consecutive passes from overlapping.
-//   load:         stage the tile from src; otherwise it is already in shared
-//                 memory (a run whose whole state stays on chip: c = n, d = 0);
-//   store_global: the last round writes to dst; otherwise back to the tile.
-// GEN = false (the single-window kernel): load and store_global are true and
-// the block has exactly one thread per NG register groups, at most.  GEN =
-// true (the batched kernel): the flags are honoured and the block may hold
-// more threads than the tile has register groups; the surplus threads then
-// only help with the copies and tables.
-template <typename R, int G, int NG, bool GEN>
-__device__ __forceinline__ void tile_pass(const typename CT<R>::T *src, typename CT<R>::T *__restrict__ psi,
-                                          const TileParams &P, uint32_t H, int n, R kdelta, bool load_,
-                                          bool store_global_) {
-    const bool load = GEN ? load_ : true;
-    const bool store_global = GEN ? store_global_ : true;
-    using C = typename CT<R>::T;
-    constexpr int LS = sizeof(C) == 8 ? 3 : 4;  // log2 bytes per amplitude
-    extern __shared__ __align__(16) unsigned char smem[];
-    uint64_t (&nib)[4][16] = g_pass_nib;
-    uint64_t (&sub_w)[kParamSub][kMaxG] = g_pass_sub_w;
-    __syncthreads();
-    const int c = P.c, d = P.d;
-    const int B = c + d;
-    const int nsub = P.nsub, nrot = P.nrot;
-    const int tid = threadIdx.x;
-    const int lgB = 31 - __clz(blockDim.x);
-    // threads of the register rounds: at most one per NG groups
-    const int lgT = GEN ? min(lgB, B - G - (NG == 4 ? 2 : NG == 2 ? 1 : 0)) : lgB;
-    const int T = 1 << lgT;
-    const uint64_t cmask = (1ull << c) - 1;
-    C *tile = reinterpret_cast<C *>(smem);
-    KRot<R> *srec = reinterpret_cast<KRot<R> *>(smem + ((size_t)sizeof(C) << B));
-
-    uint64_t k0 = (uint64_t)H << c;
+// k0 of tile H: H << c with zero bits inserted at the pivots of V.
+__device__ __forceinline__ uint64_t coset_base(const TileParams &P, uint32_t H) {
+    const int d = P.d;
+    uint64_t k0 = (uint64_t)H << P.c;
     for (int i = 0; i < d; ++i) {
         const int p = P.piv[i];
         k0 = ((k0 >> p) << (p + 1)) | (k0 & ((1ull << p) - 1));
     }
+    return k0;
+}
 
-    // ---- issue the tile loads: chunk ch = tid + i*blockDim (16 bytes each).
-    // When the block covers whole segments, seg = (tid >> seg_log) |
-    // (i << it_shift) and V(seg) = V(tid >> seg_log) ^ V(i << it_shift),
-    // walked in Gray order.
+// Issue the 16-byte asynchronous copies of the tile with base k0 from src
+// into the shared buffer buf (this thread's share of the 2^(B+LS-4)
+// chunks).  When the block covers whole segments, chunk tid + i * blockDim
+// lies in segment (tid >> seg_log) | (i << it_shift), and V of that segment
+// is V(tid >> seg_log) ^ V(i << it_shift), walked in Gray order.
+template <typename R, bool GEN>
+__device__ __forceinline__ void issue_tile_loads(const typename CT<R>::T *src, unsigned char *buf, const TileParams &P,
+                                                 uint64_t k0, int n, int tid, int lgB) {
+    constexpr int LS = sizeof(typename CT<R>::T) == 8 ? 3 : 4;  // log2 bytes per amplitude
+    const int c = P.c;
+    const int B = c + P.d;
     const int seg_log = c + LS - 4;
     const int lgchunks = B + LS - 4;
     const char *gbase = reinterpret_cast<const char *>(src);
-    if (!load) {
-    } else if (lgB >= seg_log && (!GEN || lgchunks >= lgB)) {
+    if (lgB >= seg_log && (!GEN || lgchunks >= lgB)) {
         const int niter = 1 << (lgchunks - lgB);
         const int it_shift = lgB - seg_log;
         const uint64_t base = k0 ^ v_of(P, (uint32_t)tid >> seg_log);
@@ -273,7 +257,7 @@ __device__ __forceinline__ void tile_pass(const typename CT<R>::T *src, typename
                 else if (i)
                     vi ^= (uint32_t)P.v[it_shift + (__ffs(i) - 1)];
                 const int gi = i ^ (i >> 1);
-                cp_async16(smem + (size_t)(tid + (gi << lgB)) * 16, gb + (uint64_t)(b32 ^ vi) * (1u << LS));
+                cp_async16(buf + (size_t)(tid + (gi << lgB)) * 16, gb + (uint64_t)(b32 ^ vi) * (1u << LS));
             }
         } else {
             uint64_t vi = 0;
@@ -285,16 +269,21 @@ __device__ __forceinline__ void tile_pass(const typename CT<R>::T *src, typename
                 else if (i)
                     vi ^= P.v[it_shift + (__ffs(i) - 1)];
                 const int gi = i ^ (i >> 1);
-                cp_async16(smem + (size_t)(tid + (gi << lgB)) * 16, gbase + ((base ^ vi) << LS) + off);
+                cp_async16(buf + (size_t)(tid + (gi << lgB)) * 16, gbase + ((base ^ vi) << LS) + off);
             }
         }
     } else {
         for (uint32_t ch = (uint32_t)tid; ch < (1u << lgchunks); ch += blockDim.x)
-            cp_async16(smem + (size_t)ch * 16,
+            cp_async16(buf + (size_t)ch * 16,
                        gbase + ((k0 ^ v_of(P, ch >> seg_log)) << LS) + ((uint64_t)(ch & ((1u << seg_log) - 1)) << 4));
     }
+}
 
-    // ---- per-window tables while the copies are in flight
+// The window's coset-independent tables: g_pass_nib and g_pass_sub_w.
+template <int G>
+__device__ __forceinline__ void build_window_tables(const TileParams &P, int tid) {
+    const int c = P.c, d = P.d;
+    const uint64_t cmask = (1ull << c) - 1;
     for (int e = tid; e < 64; e += blockDim.x) {
         const int k = e >> 4, jj = e & 15;
         uint64_t acc = 0;
@@ -303,15 +292,26 @@ __device__ __forceinline__ void tile_pass(const typename CT<R>::T *src, typename
             const int bi = 4 * k + i;
             if (((jj >> i) & 1) && bi < d) acc ^= P.v[bi];
         }
-        nib[k][jj] = acc;
+        g_pass_nib[k][jj] = acc;
     }
-    for (int e = tid; e < nrot * 32; e += blockDim.x) {
+    for (int e = tid; e < P.nsub * G; e += blockDim.x) {
+        const int si = e / G, i = e % G;
+        const uint32_t u = P.sub[si].u[i];
+        g_pass_sub_w[si][i] = v_of(P, u >> c) ^ ((uint64_t)u & cmask);
+    }
+}
+
+// The per-rotation records of the tile with base k0.  Coefficient i of
+// rotation r (of pair base i, or amplitude i when the group X mask is zero)
+// is signed by parity(U(m) & zt) and by the coset's parity(k0 & z), so a
+// thread only adds parity(j0 & zt).
+template <typename R>
+__device__ __forceinline__ void build_records(const TileParams &P, uint64_t k0, KRot<R> *srec, int tid) {
+    for (int e = tid; e < P.nrot * 32; e += blockDim.x) {
         const int r = e >> 5, i = e & 31;
         const TileRotP &rp = P.rot[r];
         const int mu = rp.meta & 31;
         const int m = mu ? (int)insert_zero((uint64_t)i, 31 - __clz(mu)) : i;
-        // coefficient of pair base (or amplitude) i, signed by parity(U(m) & zt)
-        // and by this coset's parity(k0 & z), so a thread only adds parity(j0 & zt)
         const uint32_t sgn = ((rp.smask >> m) ^ (uint32_t)__popcll(k0 & rp.z)) & 1u;
         srec[r].coef[i] = (m < 32) ? xsign((R)rp.base, sgn << 31) : R(0);
         if (i == 0) {
@@ -321,14 +321,25 @@ __device__ __forceinline__ void tile_pass(const typename CT<R>::T *src, typename
             srec[r].meta = rp.meta;
         }
     }
-    for (int e = tid; e < nsub * G; e += blockDim.x) {
-        const int si = e / G, i = e % G;
-        const uint32_t u = P.sub[si].u[i];
-        sub_w[si][i] = v_of(P, u >> c) ^ ((uint64_t)u & cmask);
-    }
-    cp_async_wait_all();
-    __syncthreads();
+}
 
+// The register rounds of the tile with base k0, held in the shared buffer
+// buf, with records srec and the window tables already built.  The first T
+// = 2^lgT threads take part (GEN = false: all of them).  store_global: the
+// last round writes to psi; otherwise back to buf.
+template <typename R, int G, int NG, bool GEN, bool UNI>
+__device__ __forceinline__ void tile_rounds(unsigned char *buf, const KRot<R> *srec,
+                                            typename CT<R>::T *__restrict__ psi, const TileParams &P, uint64_t k0,
+                                            int n, R kdelta, bool store_global, int tid, int lgT) {
+    using C = typename CT<R>::T;
+    constexpr int LS = sizeof(C) == 8 ? 3 : 4;  // log2 bytes per amplitude
+    uint64_t (&nib)[4][16] = g_pass_nib;
+    uint64_t (&sub_w)[kParamSub][kMaxG] = g_pass_sub_w;
+    const int c = P.c;
+    const int B = c + P.d;
+    const int nsub = P.nsub;
+    const int T = 1 << lgT;
+    const uint64_t cmask = (1ull << c) - 1;
     auto vof = [&](uint32_t seg) {
         return nib[0][seg & 15] ^ nib[1][(seg >> 4) & 15] ^ nib[2][(seg >> 8) & 15] ^ nib[3][(seg >> 12) & 15];
     };
@@ -351,10 +362,6 @@ __device__ __forceinline__ void tile_pass(const typename CT<R>::T *src, typename
         }
         const int r0 = (int)((d1.z >> 8) & 0xffu), r1 = (int)((d1.z >> 16) & 0xffu);
         const int fast_k = (int)(d1.z >> 24);
-        // One batch of NG register groups: load from the tile, rotate, store.
-        // A full standard round (K = G rotations, the common case) gets its
-        // own copy of the whole body so its registers never meet the general
-        // path's at a join; every other round runs the per-rotation dispatch.
         // Coset representatives: zero bits inserted at the round's pivots.  The
         // insertion is linear over XOR and q = tid | (group << lgT) splits into
         // disjoint fields, so j0 = spread(tid) ^ spread(group << lgT).
@@ -369,10 +376,40 @@ __device__ __forceinline__ void tile_pass(const typename CT<R>::T *src, typename
             return q;
         };
         const uint32_t j_tid = spread((uint32_t)tid);
+        // With the window in parameter space (UNI) the per-round offsets below
+        // are warp-uniform and cost no per-thread registers: group g of a
+        // batch adds spread(g << lgT) (g < NG sits below the batch bits) and,
+        // in HBM, that offset's W (idx is affine in the tile index).  A window
+        // read from shared memory recomputes both per group instead.
+        uint32_t jg[NG];
+        uint64_t wg[NG];
+#pragma unroll
+        for (int g = 0; g < NG; ++g) {
+            jg[g] = (UNI && g) ? spread((uint32_t)g << lgT) : 0u;
+            wg[g] = (UNI && g && last) ? (vof(jg[g] >> c) ^ ((uint64_t)jg[g] & cmask)) : 0ull;
+        }
         // byte offsets of the group basis in the tile (shared) and in HBM (last round)
         uint32_t ubb[G];
 #pragma unroll
         for (int i = 0; i < G; ++i) ubb[i] = ub[i] << LS;
+        // UNI also tabulates the offsets of every group member,
+        // um[m] = byte offset of U(m) and wm[m] = W(m) in HBM, so that each
+        // address is one XOR of independent operands rather than a step of a
+        // dependent Gray-code walk.
+        uint32_t um[1 << G];
+        uint64_t wm[1 << G];
+        if constexpr (UNI) {
+            uint64_t W[G];
+#pragma unroll
+            for (int i = 0; i < G; ++i) W[i] = last ? (v_of(P, ub[i] >> c) ^ ((uint64_t)ub[i] & cmask)) : 0ull;
+            um[0] = 0u;
+            wm[0] = 0ull;
+#pragma unroll
+            for (int m = 1; m < (1 << G); ++m) {
+                um[m] = um[m & (m - 1)] ^ ubb[ctz_const(m)];
+                wm[m] = wm[m & (m - 1)] ^ W[ctz_const(m)];
+            }
+        }
         // One batch of NG register groups: load from the tile, rotate, store.
         // A full standard round (K = G rotations, the common case) gets its
         // own copy of the whole body so its registers never meet the general
@@ -380,17 +417,23 @@ __device__ __forceinline__ void tile_pass(const typename CT<R>::T *src, typename
         auto batch = [&](int bt, auto mode) {
             constexpr int K = decltype(mode)::value;
             uint32_t j0[NG];
+            j0[0] = j_tid ^ spread((uint32_t)(bt * NG) << lgT);
 #pragma unroll
-            for (int g = 0; g < NG; ++g) j0[g] = j_tid ^ spread((uint32_t)(bt * NG + g) << lgT);
+            for (int g = 1; g < NG; ++g) j0[g] = UNI ? j0[0] ^ jg[g] : j_tid ^ spread((uint32_t)(bt * NG + g) << lgT);
             C a[NG][1 << G];
 #pragma unroll
             for (int g = 0; g < NG; ++g) {
                 uint32_t tb = j0[g] << LS;
-                a[g][0] = *reinterpret_cast<const C *>(smem + tb);
+                if constexpr (UNI) {
 #pragma unroll
-                for (int i = 1; i < (1 << G); ++i) {
-                    tb ^= ubb[ctz_const(i)];
-                    a[g][i ^ (i >> 1)] = *reinterpret_cast<const C *>(smem + tb);
+                    for (int m = 0; m < (1 << G); ++m) a[g][m] = *reinterpret_cast<const C *>(buf + (tb ^ um[m]));
+                } else {
+                    a[g][0] = *reinterpret_cast<const C *>(buf + tb);
+#pragma unroll
+                    for (int i = 1; i < (1 << G); ++i) {
+                        tb ^= ubb[ctz_const(i)];
+                        a[g][i ^ (i >> 1)] = *reinterpret_cast<const C *>(buf + tb);
+                    }
                 }
             }
             if constexpr (K > 0) {
@@ -420,28 +463,41 @@ __device__ __forceinline__ void tile_pass(const typename CT<R>::T *src, typename
                     uint32_t wb[G];
 #pragma unroll
                     for (int i = 0; i < G; ++i) wb[i] = (uint32_t)sub_w[si][i];
+                    const uint32_t gi0 = (uint32_t)(k0 ^ vof(j0[0] >> c)) ^ (j0[0] & (uint32_t)cmask);
 #pragma unroll
                     for (int g = 0; g < NG; ++g) {
-                        uint32_t gi = (uint32_t)(k0 ^ vof(j0[g] >> c)) ^ (j0[g] & (uint32_t)cmask);
-                        psi[gi] = a[g][0];
+                        uint32_t gi = UNI ? gi0 ^ (uint32_t)wg[g]
+                                          : (uint32_t)(k0 ^ vof(j0[g] >> c)) ^ (j0[g] & (uint32_t)cmask);
+                        if constexpr (UNI) {
 #pragma unroll
-                        for (int i = 1; i < (1 << G); ++i) {
-                            gi ^= wb[ctz_const(i)];
-                            psi[gi] = a[g][i ^ (i >> 1)];
+                            for (int m = 0; m < (1 << G); ++m) psi[gi ^ (uint32_t)wm[m]] = a[g][m];
+                        } else {
+                            psi[gi] = a[g][0];
+#pragma unroll
+                            for (int i = 1; i < (1 << G); ++i) {
+                                gi ^= wb[ctz_const(i)];
+                                psi[gi] = a[g][i ^ (i >> 1)];
+                            }
                         }
                     }
                 } else {
                     uint64_t wb[G];
 #pragma unroll
                     for (int i = 0; i < G; ++i) wb[i] = sub_w[si][i];
+                    const uint64_t gi0 = k0 ^ vof(j0[0] >> c) ^ ((uint64_t)j0[0] & cmask);
 #pragma unroll
                     for (int g = 0; g < NG; ++g) {
-                        uint64_t gi = k0 ^ vof(j0[g] >> c) ^ ((uint64_t)j0[g] & cmask);
-                        psi[gi] = a[g][0];
+                        uint64_t gi = UNI ? gi0 ^ wg[g] : k0 ^ vof(j0[g] >> c) ^ ((uint64_t)j0[g] & cmask);
+                        if constexpr (UNI) {
 #pragma unroll
-                        for (int i = 1; i < (1 << G); ++i) {
-                            gi ^= wb[ctz_const(i)];
-                            psi[gi] = a[g][i ^ (i >> 1)];
+                            for (int m = 0; m < (1 << G); ++m) psi[gi ^ wm[m]] = a[g][m];
+                        } else {
+                            psi[gi] = a[g][0];
+#pragma unroll
+                            for (int i = 1; i < (1 << G); ++i) {
+                                gi ^= wb[ctz_const(i)];
+                                psi[gi] = a[g][i ^ (i >> 1)];
+                            }
                         }
                     }
                 }
@@ -449,11 +505,16 @@ __device__ __forceinline__ void tile_pass(const typename CT<R>::T *src, typename
 #pragma unroll
                 for (int g = 0; g < NG; ++g) {
                     uint32_t tb = j0[g] << LS;
-                    *reinterpret_cast<C *>(smem + tb) = a[g][0];
+                    if constexpr (UNI) {
 #pragma unroll
-                    for (int i = 1; i < (1 << G); ++i) {
-                        tb ^= ubb[ctz_const(i)];
-                        *reinterpret_cast<C *>(smem + tb) = a[g][i ^ (i >> 1)];
+                        for (int m = 0; m < (1 << G); ++m) *reinterpret_cast<C *>(buf + (tb ^ um[m])) = a[g][m];
+                    } else {
+                        *reinterpret_cast<C *>(buf + tb) = a[g][0];
+#pragma unroll
+                        for (int i = 1; i < (1 << G); ++i) {
+                            tb ^= ubb[ctz_const(i)];
+                            *reinterpret_cast<C *>(buf + tb) = a[g][i ^ (i >> 1)];
+                        }
                     }
                 }
             }
@@ -469,6 +530,43 @@ __device__ __forceinline__ void tile_pass(const typename CT<R>::T *src, typename
         }
         if (!last || !store_global) __syncthreads();
     }
+}
+
+// One tile pass: coset H of the window P (n-qubit state), read from src and
+// written to psi (the same buffer for an in-place pass).  Used by k_tile (one
+// tile per CTA) and by the batched kernel (many tiles per CTA); the leading
+// barrier keeps a CTA's consecutive passes from overlapping.
+//   load:         stage the tile from src; otherwise it is already in shared
+//                 memory (a run whose whole state stays on chip: c = n, d = 0);
+//   store_global: the last round writes to psi; otherwise back to the tile.
+// GEN = false (the single-window kernel): load and store_global are true and
+// the block has exactly one thread per NG register groups, at most.  GEN =
+// true (the batched kernel): the flags are honoured and the block may hold
+// more threads than the tile has register groups; the surplus threads then
+// only help with the copies and tables.
+template <typename R, int G, int NG, bool GEN, bool UNI = false>
+__device__ __forceinline__ void tile_pass(const typename CT<R>::T *src, typename CT<R>::T *__restrict__ psi,
+                                          const TileParams &P, uint32_t H, int n, R kdelta, bool load_,
+                                          bool store_global_) {
+    const bool load = GEN ? load_ : true;
+    const bool store_global = GEN ? store_global_ : true;
+    using C = typename CT<R>::T;
+    extern __shared__ __align__(16) unsigned char smem[];
+    __syncthreads();
+    const int B = P.c + P.d;
+    const int tid = threadIdx.x;
+    const int lgB = 31 - __clz(blockDim.x);
+    // threads of the register rounds: at most one per NG groups
+    const int lgT = GEN ? min(lgB, B - G - (NG == 4 ? 2 : NG == 2 ? 1 : 0)) : lgB;
+    KRot<R> *srec = reinterpret_cast<KRot<R> *>(smem + ((size_t)sizeof(C) << B));
+    const uint64_t k0 = coset_base(P, H);
+    if (load) issue_tile_loads<R, GEN>(src, smem, P, k0, n, tid, lgB);
+    // the tables while the copies are in flight
+    build_window_tables<G>(P, tid);
+    build_records<R>(P, k0, srec, tid);
+    cp_async_wait_all();
+    __syncthreads();
+    tile_rounds<R, G, NG, GEN, UNI>(smem, srec, psi, P, k0, n, kdelta, store_global, tid, lgT);
 }
 
 }  // namespace ps

@@ -71,6 +71,9 @@ TUNINGS = [
     {"reg_groups": 2, "group_bits": 4},
     {"reg_groups": 4, "group_bits": 2, "tile_bits": 11},
     {"group_bits": 5, "tile_bits": 9, "max_window": 7},
+    {"seg_bits": 1, "tile_bits": 10},       # 2-amplitude segments
+    {"seg_bits": 2, "group_bits": 4, "reg_groups": 1, "tile_bits": 11},
+    {"seg_bits": 3, "tile_bits": 9},
 ]
 
 
@@ -151,6 +154,55 @@ def test_fused_equals_rotation_by_rotation(dtype):
     tile_only, _, _ = run_rotations(n, dtype, psi0, x, z, phi, {"max_window": 1, "pair_single": 2})
     assert rel(fused, unfused) < (1e-14 if dtype == ps.PS_C128 else 2e-6)
     assert np.array_equal(unfused, tile_only)
+
+
+@pytest.mark.parametrize("dtype", [ps.PS_C128, ps.PS_C64])
+@pytest.mark.parametrize("tuning", [{"seg_bits": 3}, {"seg_bits": 2, "group_bits": 4, "reg_groups": 1},
+                                    {"seg_bits": 3, "group_bits": 4, "reg_groups": 1},
+                                    {"group_bits": 5, "reg_groups": 1}, {"seg_bits": 1, "group_bits": 2}, {"seg_bits": 6}])
+def test_segment_sizes_and_group_shapes_vs_oracle(dtype, tuning):
+    """JW qDRIFT (small angles, even Y counts): windows of the wider span that
+    a smaller seg_bits allows, and register rounds of G = 2, 4 and 5 (most of
+    them standard rounds), against the oracle."""
+    n = 18
+    xh, zh, hh = inputs.jw_hamiltonian(n, 400, seed=17)
+    H = ps.Hamiltonian(n, xh, zh, hh)
+    x, z, phi = H.qdrift_stream(1.0, 500, 18)
+    psi0 = inputs.gaussian_state(n, 19)
+    ref = oracle.apply(psi0, x, z, phi)
+    if dtype == ps.PS_C128 and tuning.get("group_bits") == 5:
+        tuning = dict(tuning, group_bits=4)
+    out, g, _ = run_rotations(n, dtype, psi0, x, z, phi, tuning)
+    assert rel(out, ref) < TOL[dtype]
+    assert rel_scalar(g, oracle.overlap(psi0, ref)) < TOL[dtype]
+
+
+_REF22 = {}
+
+
+@pytest.mark.parametrize("dtype", [ps.PS_C128, ps.PS_C64])
+@pytest.mark.parametrize("tuning", [{"tile_threads": 64}, {"tile_threads": 128}, {"tile_threads": 128, "reg_groups": 1},
+                                    {"tile_threads": 128, "reg_groups": 4}, {"tile_threads": 64, "reg_groups": 4},
+                                    {"tile_threads": 256, "reg_groups": 2}])
+def test_tile_threads_give_the_same_amplitudes(dtype, tuning):
+    """Fewer threads per tile (more register batches per thread) and other
+    group counts change only which thread updates which amplitude, never the
+    arithmetic: bitwise equal to the default launch, and within tolerance of
+    the oracle.  n = 22 gives 2^9 or 2^10 tiles."""
+    n = 22
+    xh, zh, hh = inputs.jw_hamiltonian(n, 300, seed=23)
+    H = ps.Hamiltonian(n, xh, zh, hh)
+    x, z, phi = H.qdrift_stream(1.0, 160, 24)
+    psi0 = inputs.gaussian_state(n, 25)
+    if dtype == ps.PS_C128:
+        tuning = dict(tuning, reg_groups=min(tuning.get("reg_groups", 1), 2))
+    out, g, _ = run_rotations(n, dtype, psi0, x, z, phi, tuning)
+    base, g0, _ = run_rotations(n, dtype, psi0, x, z, phi)
+    assert np.array_equal(out, base)
+    assert g == g0
+    if n not in _REF22:
+        _REF22[n] = oracle.apply(psi0, x, z, phi)
+    assert rel(out, _REF22[n]) < TOL[dtype]
 
 
 @pytest.mark.parametrize("dtype", [ps.PS_C128, ps.PS_C64])

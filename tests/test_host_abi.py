@@ -41,7 +41,7 @@ def test_every_declared_symbol_is_exported():
 
 
 def test_abi_version_and_empty_error():
-    assert ps.ps_abi_version() == 1
+    assert ps.ps_abi_version() == 2
     assert isinstance(ps.ps_last_error(), str)
 
 
@@ -87,6 +87,10 @@ def test_plan_validation():
         ps.ps_plan_describe(20, ps.PS_C64, [1], [0], [0.1], {"group_bits": 6})
     with pytest.raises(ps.PsError):
         ps.ps_plan_describe(20, ps.PS_C64, [1], [0], [0.1], {"max_window": 300})
+    with pytest.raises(ps.PsError):
+        ps.ps_plan_describe(20, ps.PS_C64, [1], [0], [0.1], {"seg_bits": 14})
+    with pytest.raises(ps.PsError):
+        ps.ps_plan_describe(20, ps.PS_C64, [1], [0], [0.1], {"tile_bits": 10, "seg_bits": 11})
     info = ps.ps_plan_describe(20, ps.PS_C64, [], [], [])
     assert info["windows"] == 0
 
@@ -243,6 +247,28 @@ def test_scheduler_jw_qdrift_fuses_many_rotations_per_pass():
             continue
         vecs = [int(x[j]) >> 4 for j in members] + [int(x[members[-1] + 1]) >> 4]
         assert _rank(vecs) > B - 4
+
+
+@pytest.mark.parametrize("seg_bits", [1, 2, 3, 4])
+def test_scheduler_seg_bits_bounds_the_window_span(seg_bits):
+    # c >= seg_bits in every tile window, the span above c fills the rest of
+    # the tile, and every maximal window is one rotation short of B - seg_bits + 1
+    n = 24
+    xh, zh, hh = inputs.jw_hamiltonian(n, 800, seed=13)
+    H = ps.Hamiltonian(n, xh, zh, hh)
+    x, z, phi = H.qdrift_stream(1.0, 3000, 14)
+    tun = {"seg_bits": seg_bits}
+    ex = ps.ps_plan_export(n, ps.PS_C64, x, z, phi, tun)
+    B = 13
+    for w in range(len(ex["kind"]) - 1):
+        assert ex["kind"][w] == 0 and ex["c"][w] >= seg_bits and ex["c"][w] + ex["d"][w] == B
+        members = np.flatnonzero(ex["window_of"] == w)
+        if len(members) == 32:
+            continue
+        vecs = [int(x[j]) >> seg_bits for j in members] + [int(x[members[-1] + 1]) >> seg_bits]
+        assert _rank(vecs) > B - seg_bits
+    rp = [ps.ps_plan_describe(n, ps.PS_C64, x, z, phi, {"seg_bits": s})["windows"] for s in (4, 2)]
+    assert rp[1] < rp[0]
 
 
 def _rank(vecs):
