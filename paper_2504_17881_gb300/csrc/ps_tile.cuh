@@ -327,7 +327,7 @@ __device__ __forceinline__ void build_records(const TileParams &P, uint64_t k0, 
 // buf, with records srec and the window tables already built.  The first T
 // = 2^lgT threads take part (GEN = false: all of them).  store_global: the
 // last round writes to psi; otherwise back to buf.
-template <typename R, int G, int NG, bool GEN, bool UNI>
+template <typename R, int G, int NG, bool GEN>
 __device__ __forceinline__ void tile_rounds(unsigned char *buf, const KRot<R> *srec,
                                             typename CT<R>::T *__restrict__ psi, const TileParams &P, uint64_t k0,
                                             int n, R kdelta, bool store_global, int tid, int lgT) {
@@ -376,40 +376,10 @@ __device__ __forceinline__ void tile_rounds(unsigned char *buf, const KRot<R> *s
             return q;
         };
         const uint32_t j_tid = spread((uint32_t)tid);
-        // With the window in parameter space (UNI) the per-round offsets below
-        // are warp-uniform and cost no per-thread registers: group g of a
-        // batch adds spread(g << lgT) (g < NG sits below the batch bits) and,
-        // in HBM, that offset's W (idx is affine in the tile index).  A window
-        // read from shared memory recomputes both per group instead.
-        uint32_t jg[NG];
-        uint64_t wg[NG];
-#pragma unroll
-        for (int g = 0; g < NG; ++g) {
-            jg[g] = (UNI && g) ? spread((uint32_t)g << lgT) : 0u;
-            wg[g] = (UNI && g && last) ? (vof(jg[g] >> c) ^ ((uint64_t)jg[g] & cmask)) : 0ull;
-        }
         // byte offsets of the group basis in the tile (shared) and in HBM (last round)
         uint32_t ubb[G];
 #pragma unroll
         for (int i = 0; i < G; ++i) ubb[i] = ub[i] << LS;
-        // UNI also tabulates the offsets of every group member,
-        // um[m] = byte offset of U(m) and wm[m] = W(m) in HBM, so that each
-        // address is one XOR of independent operands rather than a step of a
-        // dependent Gray-code walk.
-        uint32_t um[1 << G];
-        uint64_t wm[1 << G];
-        if constexpr (UNI) {
-            uint64_t W[G];
-#pragma unroll
-            for (int i = 0; i < G; ++i) W[i] = last ? (v_of(P, ub[i] >> c) ^ ((uint64_t)ub[i] & cmask)) : 0ull;
-            um[0] = 0u;
-            wm[0] = 0ull;
-#pragma unroll
-            for (int m = 1; m < (1 << G); ++m) {
-                um[m] = um[m & (m - 1)] ^ ubb[ctz_const(m)];
-                wm[m] = wm[m & (m - 1)] ^ W[ctz_const(m)];
-            }
-        }
         // One batch of NG register groups: load from the tile, rotate, store.
         // A full standard round (K = G rotations, the common case) gets its
         // own copy of the whole body so its registers never meet the general
@@ -417,23 +387,17 @@ __device__ __forceinline__ void tile_rounds(unsigned char *buf, const KRot<R> *s
         auto batch = [&](int bt, auto mode) {
             constexpr int K = decltype(mode)::value;
             uint32_t j0[NG];
-            j0[0] = j_tid ^ spread((uint32_t)(bt * NG) << lgT);
 #pragma unroll
-            for (int g = 1; g < NG; ++g) j0[g] = UNI ? j0[0] ^ jg[g] : j_tid ^ spread((uint32_t)(bt * NG + g) << lgT);
+            for (int g = 0; g < NG; ++g) j0[g] = j_tid ^ spread((uint32_t)(bt * NG + g) << lgT);
             C a[NG][1 << G];
 #pragma unroll
             for (int g = 0; g < NG; ++g) {
                 uint32_t tb = j0[g] << LS;
-                if constexpr (UNI) {
+                a[g][0] = *reinterpret_cast<const C *>(buf + tb);
 #pragma unroll
-                    for (int m = 0; m < (1 << G); ++m) a[g][m] = *reinterpret_cast<const C *>(buf + (tb ^ um[m]));
-                } else {
-                    a[g][0] = *reinterpret_cast<const C *>(buf + tb);
-#pragma unroll
-                    for (int i = 1; i < (1 << G); ++i) {
-                        tb ^= ubb[ctz_const(i)];
-                        a[g][i ^ (i >> 1)] = *reinterpret_cast<const C *>(buf + tb);
-                    }
+                for (int i = 1; i < (1 << G); ++i) {
+                    tb ^= ubb[ctz_const(i)];
+                    a[g][i ^ (i >> 1)] = *reinterpret_cast<const C *>(buf + tb);
                 }
             }
             if constexpr (K > 0) {
@@ -463,41 +427,28 @@ __device__ __forceinline__ void tile_rounds(unsigned char *buf, const KRot<R> *s
                     uint32_t wb[G];
 #pragma unroll
                     for (int i = 0; i < G; ++i) wb[i] = (uint32_t)sub_w[si][i];
-                    const uint32_t gi0 = (uint32_t)(k0 ^ vof(j0[0] >> c)) ^ (j0[0] & (uint32_t)cmask);
 #pragma unroll
                     for (int g = 0; g < NG; ++g) {
-                        uint32_t gi = UNI ? gi0 ^ (uint32_t)wg[g]
-                                          : (uint32_t)(k0 ^ vof(j0[g] >> c)) ^ (j0[g] & (uint32_t)cmask);
-                        if constexpr (UNI) {
+                        uint32_t gi = (uint32_t)(k0 ^ vof(j0[g] >> c)) ^ (j0[g] & (uint32_t)cmask);
+                        psi[gi] = a[g][0];
 #pragma unroll
-                            for (int m = 0; m < (1 << G); ++m) psi[gi ^ (uint32_t)wm[m]] = a[g][m];
-                        } else {
-                            psi[gi] = a[g][0];
-#pragma unroll
-                            for (int i = 1; i < (1 << G); ++i) {
-                                gi ^= wb[ctz_const(i)];
-                                psi[gi] = a[g][i ^ (i >> 1)];
-                            }
+                        for (int i = 1; i < (1 << G); ++i) {
+                            gi ^= wb[ctz_const(i)];
+                            psi[gi] = a[g][i ^ (i >> 1)];
                         }
                     }
                 } else {
                     uint64_t wb[G];
 #pragma unroll
                     for (int i = 0; i < G; ++i) wb[i] = sub_w[si][i];
-                    const uint64_t gi0 = k0 ^ vof(j0[0] >> c) ^ ((uint64_t)j0[0] & cmask);
 #pragma unroll
                     for (int g = 0; g < NG; ++g) {
-                        uint64_t gi = UNI ? gi0 ^ wg[g] : k0 ^ vof(j0[g] >> c) ^ ((uint64_t)j0[g] & cmask);
-                        if constexpr (UNI) {
+                        uint64_t gi = k0 ^ vof(j0[g] >> c) ^ ((uint64_t)j0[g] & cmask);
+                        psi[gi] = a[g][0];
 #pragma unroll
-                            for (int m = 0; m < (1 << G); ++m) psi[gi ^ wm[m]] = a[g][m];
-                        } else {
-                            psi[gi] = a[g][0];
-#pragma unroll
-                            for (int i = 1; i < (1 << G); ++i) {
-                                gi ^= wb[ctz_const(i)];
-                                psi[gi] = a[g][i ^ (i >> 1)];
-                            }
+                        for (int i = 1; i < (1 << G); ++i) {
+                            gi ^= wb[ctz_const(i)];
+                            psi[gi] = a[g][i ^ (i >> 1)];
                         }
                     }
                 }
@@ -505,16 +456,11 @@ __device__ __forceinline__ void tile_rounds(unsigned char *buf, const KRot<R> *s
 #pragma unroll
                 for (int g = 0; g < NG; ++g) {
                     uint32_t tb = j0[g] << LS;
-                    if constexpr (UNI) {
+                    *reinterpret_cast<C *>(buf + tb) = a[g][0];
 #pragma unroll
-                        for (int m = 0; m < (1 << G); ++m) *reinterpret_cast<C *>(buf + (tb ^ um[m])) = a[g][m];
-                    } else {
-                        *reinterpret_cast<C *>(buf + tb) = a[g][0];
-#pragma unroll
-                        for (int i = 1; i < (1 << G); ++i) {
-                            tb ^= ubb[ctz_const(i)];
-                            *reinterpret_cast<C *>(buf + tb) = a[g][i ^ (i >> 1)];
-                        }
+                    for (int i = 1; i < (1 << G); ++i) {
+                        tb ^= ubb[ctz_const(i)];
+                        *reinterpret_cast<C *>(buf + tb) = a[g][i ^ (i >> 1)];
                     }
                 }
             }
@@ -544,7 +490,7 @@ __device__ __forceinline__ void tile_rounds(unsigned char *buf, const KRot<R> *s
 // true (the batched kernel): the flags are honoured and the block may hold
 // more threads than the tile has register groups; the surplus threads then
 // only help with the copies and tables.
-template <typename R, int G, int NG, bool GEN, bool UNI = false>
+template <typename R, int G, int NG, bool GEN, bool RECORDS_FIRST = false>
 __device__ __forceinline__ void tile_pass(const typename CT<R>::T *src, typename CT<R>::T *__restrict__ psi,
                                           const TileParams &P, uint32_t H, int n, R kdelta, bool load_,
                                           bool store_global_) {
@@ -561,12 +507,19 @@ __device__ __forceinline__ void tile_pass(const typename CT<R>::T *src, typename
     KRot<R> *srec = reinterpret_cast<KRot<R> *>(smem + ((size_t)sizeof(C) << B));
     const uint64_t k0 = coset_base(P, H);
     if (load) issue_tile_loads<R, GEN>(src, smem, P, k0, n, tid, lgB);
-    // the tables while the copies are in flight
-    build_window_tables<G>(P, tid);
-    build_records<R>(P, k0, srec, tid);
+    // the tables while the copies are in flight (either order is correct; the
+    // single-window kernel builds its records first, the batched kernel its
+    // window tables first: in each the other order spills registers)
+    if constexpr (RECORDS_FIRST) {
+        build_records<R>(P, k0, srec, tid);
+        build_window_tables<G>(P, tid);
+    } else {
+        build_window_tables<G>(P, tid);
+        build_records<R>(P, k0, srec, tid);
+    }
     cp_async_wait_all();
     __syncthreads();
-    tile_rounds<R, G, NG, GEN, UNI>(smem, srec, psi, P, k0, n, kdelta, store_global, tid, lgT);
+    tile_rounds<R, G, NG, GEN>(smem, srec, psi, P, k0, n, kdelta, store_global, tid, lgT);
 }
 
 }  // namespace ps
