@@ -67,8 +67,9 @@ typedef struct ps_tuning {
     int pair_single;   /* 1: a window holding one non-diagonal rotation runs the pair-streaming
                           kernel instead of the tile kernel; 2: never; 0 = default (1) */
     int kernel_timing; /* 1: time every launch with CUDA events (read with ps_get_stats) */
-    int reg_groups;    /* register groups of 2^G amplitudes per thread: 1, 2 or 4 (default 2;
-                          capped at 32 complex64 / 16 complex128 amplitudes per thread) */
+    int reg_groups;    /* register groups of 2^G amplitudes per thread: 1, 2 or 4 (default 4 for
+                          PS_C64, 2 for PS_C128; capped at 32 complex64 / 16 complex128
+                          amplitudes per thread) */
     int seg_bits;      /* c_min: log2 of the fewest contiguous amplitudes per segment of a
                           tile, 1..B (default 4 for PS_C64, 3 for PS_C128: 128-byte
                           segments).  A smaller value leaves more tile bits for the window
