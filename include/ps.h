@@ -317,6 +317,24 @@ uint64_t ps_partial_sample_count(double delta, double lambda_R, int M);
 int ps_rpe_signal(ps_state *work, const ps_state *psi0, const ps_ham *ham, int order, size_t L_D, double delta,
                   uint32_t M, uint64_t Ns, uint64_t seed, double *Z_out);
 
+/* Robust phase estimation of the signal's dominant frequency (Methods,
+ * "Data analysis": RPE after Kimmel et al. 2015 recovers the effective
+ * ground-state energy from Z_m = g(delta 2^m)).  Z: 2 (M + 1) doubles (re,
+ * im of Z_0 .. Z_M), for example from ps_rpe_signal.  With Z_m close to
+ * c e^{i 2^m theta}:
+ *   theta_0 = arg Z_0 in (-pi, pi];
+ *   theta_m = (arg Z_m + 2 pi k) / 2^m, k = floor((2^m theta_{m-1} - arg Z_m) / (2 pi) + 1/2),
+ *             the branch nearest theta_{m-1};
+ *   *energy_out = theta_M / delta.
+ * If every round's phase error |arg Z_m - 2^m theta| (mod 2 pi) is below
+ * pi/3, every branch choice is right and theta_M - theta is round M's error
+ * divided by 2^M.  The energy is defined modulo 2 pi / delta: callers keep
+ * |delta E| < pi (shift H by a multiple of the identity if needed).
+ * theta_out (optional, M + 1 doubles) receives every round's estimate.
+ * PS_ERR_ARG for M > 62, delta zero or non-finite, or a non-finite Z.
+ * Host only. */
+int ps_rpe_estimate(const double *Z, uint32_t M, double delta, double *energy_out, double *theta_out);
+
 /* The deterministic size L_D that minimises the cost model of the
  * partially randomised method (Methods, "Hamiltonian simulation"),
  *   C_tot = a L_D / (eps delta) + b lambda_R^2 / eps^2,

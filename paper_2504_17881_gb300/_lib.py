@@ -131,6 +131,7 @@ _SIGS = {
     "ps_ham_sort_lexicographic": (_i, [_vp]),
     "ps_partial_sample_count": (_u64, [_d, _d, _i]),
     "ps_rpe_signal": (_i, [_vp, _vp, _vp, _i, _sz, _d, _u32, _u64, _u64, _vp]),
+    "ps_rpe_estimate": (_i, [_vp, _u32, _d, ctypes.POINTER(_d), _vp]),
     "ps_shard_plan": (_i, [_i, _i, _i, _vp, _vp, _vp, _sz, ctypes.POINTER(_sz), _vp, _vp, _vp, _vp, _vp]),
     "ps_partial_optimize_split": (_i, [_vp, _d, _d, _d, ctypes.POINTER(_sz), ctypes.POINTER(_d), ctypes.POINTER(_d)]),
     "ps_ham_trotter_bound": (_i, [_vp, _sz, ctypes.POINTER(_d)]),
@@ -664,6 +665,20 @@ def ps_rpe_signal(work: int, psi0: int, ham: int, order: int, L_D: int, delta: f
     _check(lib.ps_rpe_signal(ctypes.c_void_p(work), ctypes.c_void_p(psi0), ctypes.c_void_p(ham), order, L_D, delta,
                              M, Ns, seed, _ptr(out)))
     return out[0::2] + 1j * out[1::2]
+
+
+def ps_rpe_estimate(Z, delta: float):
+    """(energy, per-round phase estimates) from the complex signal Z_0..Z_M."""
+    Z = np.asarray(Z, dtype=np.complex128).ravel()
+    if Z.size == 0:
+        raise ValueError("the signal needs at least Z_0")
+    buf = np.empty(2 * Z.size, dtype=np.float64)
+    buf[0::2] = Z.real
+    buf[1::2] = Z.imag
+    theta = np.zeros(Z.size, dtype=np.float64)
+    e = _d()
+    _check(lib.ps_rpe_estimate(_ptr(buf), Z.size - 1, delta, ctypes.byref(e), _ptr(theta)))
+    return e.value, theta
 
 
 def ps_partial_optimize_split(ham: int, eps: float, a: float, b: float):

@@ -306,6 +306,28 @@ int ps_rpe_signal(ps_state *work, const ps_state *psi0, const ps_ham *ham, int o
     return PS_OK;
 }
 
+int ps_rpe_estimate(const double *Z, uint32_t M, double delta, double *energy_out, double *theta_out) {
+    if (!Z || !energy_out) return lfail(PS_ERR_ARG, "null argument");
+    if (M > 62) return lfail(PS_ERR_ARG, "M must be at most 62");
+    if (!std::isfinite(delta) || delta == 0.0) return lfail(PS_ERR_ARG, "delta must be finite and nonzero");
+    for (uint32_t m = 0; m <= M; ++m)
+        if (!std::isfinite(Z[2 * m]) || !std::isfinite(Z[2 * m + 1])) return lfail(PS_ERR_ARG, "non-finite signal");
+    const double two_pi = 2.0 * M_PI;
+    // round 0 fixes the branch of theta in (-pi, pi]; round m sees 2^m theta
+    // modulo 2 pi and keeps the branch nearest the previous estimate
+    double theta = std::atan2(Z[1], Z[0]);
+    if (theta_out) theta_out[0] = theta;
+    for (uint32_t m = 1; m <= M; ++m) {
+        const double scale = std::ldexp(1.0, (int)m);
+        const double phase = std::atan2(Z[2 * m + 1], Z[2 * m]);
+        const double k = std::floor((scale * theta - phase) / two_pi + 0.5);
+        theta = (phase + two_pi * k) / scale;
+        if (theta_out) theta_out[m] = theta;
+    }
+    *energy_out = theta / delta;
+    return PS_OK;
+}
+
 int ps_partial_optimize_split(const ps_ham *ham, double eps, double a, double b, size_t *L_D_out, double *delta_out,
                               double *cost_out) {
     if (!ham || !L_D_out) return lfail(PS_ERR_ARG, "null argument");

@@ -479,3 +479,34 @@ def test_rpe_signal_reuses_state_and_matches_separate_runs(order, L_D, Ns):
             ref = oracle.partial2(psi0, x, z, h, L_D, t, steps, Ns, seed)
         g = np.vdot(psi0, ref)
         assert abs(Z[m] - g) < 1e-12, (m, Z[m], g)
+
+
+@pytest.mark.parametrize("dtype,tol", [(ps.PS_C128, 1e-11), (ps.PS_C64, 1e-4)])
+def test_rpe_signal_and_estimate_recover_the_trotter_eigenphase(dtype, tol):
+    """The RPE chain on the GPU: the signal of a state mostly along one
+    eigenvector of the first-order step U(delta) (n = 5, dense U from the
+    oracle), then ps_rpe_estimate, gives that eigenvector's phase."""
+    from oracle import rpe as OR
+    n, delta, M = 5, 0.15, 8
+    x, z, h = inputs.jw_hamiltonian(n, 16, seed=33, lam=3.0)
+    dim = 1 << n
+    U = np.zeros((dim, dim), dtype=np.complex128)
+    for k in range(dim):
+        e = np.zeros(dim, dtype=np.complex128)
+        e[k] = 1.0
+        U[:, k] = oracle.trotter(e, x, z, h, delta, 1)
+    _, vecs = np.linalg.eigh((U + U.conj().T) / 2 + 0.37 * (U - U.conj().T) / 2j)
+    v0 = vecs[:, 0]
+    theta0 = np.angle(v0.conj() @ U @ v0)
+    w = np.random.default_rng(34).normal(size=dim) + 0j
+    w -= (v0.conj() @ w) * v0
+    w /= np.linalg.norm(w)
+    psi0 = np.sqrt(0.85) * v0 + np.sqrt(0.15) * w
+    H = ps.Hamiltonian(n, x, z, h)
+    p0 = gpu_state(n, dtype, psi0)
+    work = gpu_state(n, dtype, psi0)
+    Z = ps.ps_rpe_signal(work.handle, p0.handle, H.handle, 1, H.L, delta, M)
+    Z_ref = OR.signal(psi0, x, z, h, delta, M)
+    assert np.max(np.abs(Z - Z_ref)) < tol
+    E, _ = ps.ps_rpe_estimate(Z, delta)
+    assert abs(E * delta - theta0) <= np.arcsin(0.15 / 0.85) / 2.0 ** M + 1e-9
