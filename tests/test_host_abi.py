@@ -156,7 +156,7 @@ def _check_plan(n, dtype, x, z, phi, tuning=None):
     tun = {"tile_bits": 13 if dtype == ps.PS_C64 else 12, "max_window": 64}
     tun.update(tuning or {})
     B = min(tun["tile_bits"], n)
-    cmin = min(4 if dtype == ps.PS_C64 else 3, B)
+    cmin = min(tun.get("seg_bits", 4 if dtype == ps.PS_C64 else 3), B)
     wo = ex["window_of"]
     m = len(x)
     assert np.all(np.diff(wo.astype(np.int64)) >= 0) and (m == 0 or wo[0] == 0)
@@ -288,6 +288,23 @@ def test_scheduler_model_matches_oracle(n, B):
     psi, got = _apply_plan_model(n, x, z, phi, ex, Bu)
     ref = oracle.apply(psi, x, z, phi)
     assert np.max(np.abs(got - ref)) < 1e-12
+
+
+@pytest.mark.parametrize("n,B,seg", [(10, 8, 1), (11, 9, 2), (12, 10, 3), (12, 9, 5), (13, 11, 2)])
+def test_scheduler_model_with_segment_sizes(n, B, seg):
+    # JW qDRIFT windows at every segment size: the exported windows, applied
+    # coset by coset in tile coordinates, reproduce the oracle's evolution
+    x, z, h, H = _ham(n, 60, 40 + n + seg)
+    xs, zs, ph = H.qdrift_stream(1.0, 240, 41 + seg)
+    ex, Bu = _check_plan(n, ps.PS_C64, xs, zs, ph, {"tile_bits": B, "seg_bits": seg, "max_window": 32})
+    psi, got = _apply_plan_model(n, xs, zs, ph, ex, Bu)
+    ref = oracle.apply(psi, xs, zs, ph)
+    assert np.max(np.abs(got - ref)) < 1e-12
+    # a smaller segment leaves more of the tile to the span: never fewer rotations per window
+    info = ps.ps_plan_describe(n, ps.PS_C64, xs, zs, ph, {"tile_bits": B, "seg_bits": seg})
+    if seg < min(4, B):
+        wider = ps.ps_plan_describe(n, ps.PS_C64, xs, zs, ph, {"tile_bits": B, "seg_bits": min(4, B)})
+        assert info["windows"] <= wider["windows"]
 
 
 def test_second_order_streams_reproduce_oracle_drivers():
