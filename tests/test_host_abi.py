@@ -91,6 +91,11 @@ def test_plan_validation():
         ps.ps_plan_describe(20, ps.PS_C64, [1], [0], [0.1], {"seg_bits": 14})
     with pytest.raises(ps.PsError):
         ps.ps_plan_describe(20, ps.PS_C64, [1], [0], [0.1], {"tile_bits": 10, "seg_bits": 11})
+    for bad in (32, 96, 1024):
+        with pytest.raises(ps.PsError):
+            ps.ps_plan_describe(20, ps.PS_C64, [1], [0], [0.1], {"tile_threads": bad})
+    for good in (64, 128, 256, 512):
+        ps.ps_plan_describe(20, ps.PS_C64, [1], [0], [0.1], {"tile_threads": good})
     info = ps.ps_plan_describe(20, ps.PS_C64, [], [], [])
     assert info["windows"] == 0
 
