@@ -44,8 +44,10 @@ QDRIFT_SEED = 4
 PSI0_SEED = 11
 SEGMENTS = 10
 SEG_LEN = N_SAMPLES // SEGMENTS
-FP64_PREFIX = 1000
-CPU_SAMPLE_ROTATIONS = 2
+FP64_PREFIX = SEG_LEN
+CPU_ROTATIONS_1T = 2      # oracle sample, one thread
+CPU_ROTATIONS_MT = 8      # oracle sample, all host cores
+REF_ROTATIONS_PER_STEP = 4
 FALLBACK_HBM_GBS = 6800.0
 BATCH_RUNS = 512
 BATCH_SEED = 5
@@ -66,6 +68,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--fp64-rotations", type=int, default=SEG_LEN,
+                    help="rotations of the stream run in complex128 and complex64 for the error report "
+                         "(default one segment; 100000 for the whole run)")
     ap.add_argument("--workload", choices=["qdrift30", "batched", "learned"], default="qdrift30",
                     help="batched: 512 independent qDRIFT / partially randomised runs, n 14..22, in one "
                          "persistent launch (reported on its own JSON line)")
@@ -187,32 +192,95 @@ def aggregate_ranks(dist, device, elapsed_ms: float, units: int, launches: int):
 
 
 def make_workload(rank: int):
-    from paper_2504_17881_gb300 import inputs
+    inputs = load_inputs()
     x, z, h = inputs.jw_hamiltonian(N_QUBITS, N_TERMS, seed=HAM_SEED)
     idx, amp = inputs.determinant_state(N_QUBITS, seed=PSI0_SEED)
     return x, z, h, idx, amp, QDRIFT_SEED + rank
 
 
-def cpu_baseline_sample(rotations: int):
-    """Time the oracle (complex128, single thread) on the first `rotations` of the stream."""
-    import oracle
-    from paper_2504_17881_gb300 import inputs
-    x, z, h = inputs.jw_hamiltonian(N_QUBITS, N_TERMS, seed=HAM_SEED)
-    idx = oracle.qdrift_indices(h, QDRIFT_SEED, 0, rotations).astype(np.int64)
-    lam = 0.0
-    for v in h:
-        lam += abs(float(v))
-    tau = lam * T_TOTAL / N_SAMPLES
-    xs, zs = x[idx], z[idx]
-    ph = np.where(h[idx] > 0, tau, -tau)
-    sidx, samp = inputs.determinant_state(N_QUBITS, seed=PSI0_SEED)
-    psi = np.zeros(1 << N_QUBITS, dtype=np.complex128)
-    psi[sidx.astype(np.int64)] = samp
-    tmp = np.zeros_like(psi)
-    t0 = time.perf_counter()
-    oracle.apply_inplace(psi, tmp, xs, zs, ph)
-    dt = time.perf_counter() - t0
-    return rotations / dt, dt
+def load_inputs():
+    """The seeded input generators, loaded by file path: the oracle legs must
+    not import the package (its __init__ opens libps)."""
+    import importlib.util
+    spec = importlib.util.spec_from_file_location(
+        "_ps_inputs", os.path.join(ROOT, "paper_2504_17881_gb300", "inputs.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
+class OracleRun:
+    """The oracle (complex128 scatter form) walking the benchmark's qDRIFT
+    stream from the 8-determinant state, with its own sampler."""
+
+    def __init__(self, total_rotations: int):
+        import oracle
+        inputs = load_inputs()
+        self.oracle = oracle
+        x, z, h = inputs.jw_hamiltonian(N_QUBITS, N_TERMS, seed=HAM_SEED)
+        idx = oracle.qdrift_indices(h, QDRIFT_SEED, 0, total_rotations).astype(np.int64)
+        lam = 0.0
+        for v in h:
+            lam += abs(float(v))
+        tau = lam * T_TOTAL / N_SAMPLES
+        self.xs, self.zs = x[idx], z[idx]
+        self.ph = np.where(h[idx] > 0, tau, -tau)
+        self.sidx, self.samp = inputs.determinant_state(N_QUBITS, seed=PSI0_SEED)
+        self.psi0 = np.zeros(1 << N_QUBITS, dtype=np.complex128)
+        self.psi0[self.sidx.astype(np.int64)] = self.samp
+        self.psi = self.psi0.copy()
+        self.tmp = np.empty_like(self.psi)
+        self.tmp.fill(0)  # touch every page before any timing
+
+    def reset(self):
+        np.copyto(self.psi, self.psi0)
+
+    def apply(self, first: int, count: int, threads: int) -> float:
+        """Rotations [first, first + count) on the current state; seconds taken."""
+        self.oracle.set_threads(threads)
+        try:
+            t0 = time.perf_counter()
+            self.oracle.apply_inplace(self.psi, self.tmp, self.xs[first:first + count],
+                                      self.zs[first:first + count], self.ph[first:first + count])
+            return time.perf_counter() - t0
+        finally:
+            self.oracle.set_threads(1)
+
+    def overlap(self, threads: int) -> complex:
+        self.oracle.set_threads(threads)
+        try:
+            return self.oracle.overlap(self.psi0, self.psi)
+        finally:
+            self.oracle.set_threads(1)
+
+
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:  # pragma: no cover
+        return os.cpu_count() or 1
+
+
+def cpu_baseline_leg():
+    """The oracle as it stands on this host: the first rotations of the same
+    stream at n = 30, once on one thread and once on every host core."""
+    cores = host_cores()
+    try:
+        import oracle
+        run = OracleRun(max(CPU_ROTATIONS_1T, CPU_ROTATIONS_MT))
+        dt1 = run.apply(0, CPU_ROTATIONS_1T, 1)
+        run.reset()
+        dtm = run.apply(0, CPU_ROTATIONS_MT, cores)
+        threads = cores if oracle.has_openmp() else 1
+        del run
+    except Exception as e:  # noqa: BLE001
+        return {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "error": str(e)}
+    return {"value": CPU_ROTATIONS_MT / dtm, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"first {CPU_ROTATIONS_MT} rotations of the same qDRIFT stream at n={N_QUBITS} "
+                      f"(complex128 scatter-form oracle, OpenMP over {threads} threads, {dtm:.1f} s)",
+            "single_thread": {"value": CPU_ROTATIONS_1T / dt1, "unit": UNIT, "cores": 1,
+                              "sample": f"first {CPU_ROTATIONS_1T} rotations, 1 thread ({dt1:.1f} s)"},
+            "host_cores_available": cores}
 
 
 # ------------------------------------------------------------------- ours
@@ -297,42 +365,52 @@ def run_ours(args):
     # ------------------------------------------------------------- FP64 path
     fp64 = None
     if not args.no_fp64:
-        xs, zs, ph = segs[0][0][:FP64_PREFIX], segs[0][1][:FP64_PREFIX], segs[0][2][:FP64_PREFIX]
-        plan64 = ps.Plan(N_QUBITS, ps.PS_C128, xs, zs, ph)
-        plan32 = ps.Plan(N_QUBITS, ps.PS_C64, xs, zs, ph)
+        nrot = max(1, min(args.fp64_rotations, N_SAMPLES))
+        nseg = (nrot + SEG_LEN - 1) // SEG_LEN
+        parts = []
+        for sidx in range(nseg):
+            cnt = min(SEG_LEN, nrot - sidx * SEG_LEN)
+            sg = segs[sidx] if sidx < len(segs) else H.qdrift_stream(T_TOTAL, N_SAMPLES, seed, first=sidx * SEG_LEN,
+                                                                     count=SEG_LEN)
+            parts.append((sg[0][:cnt], sg[1][:cnt], sg[2][:cnt]))
+        plans64 = [ps.Plan(N_QUBITS, ps.PS_C128, *pt) for pt in parts]
+        plans32 = [ps.Plan(N_QUBITS, ps.PS_C64, *pt) for pt in parts]
         p64 = ps.StateVector(N_QUBITS, dtype=torch.complex128, device=dev)
         p64_0 = ps.StateVector(N_QUBITS, dtype=torch.complex128, device=dev)
         init_state(p64.tensor)
         init_state(p64_0.tensor)
         p64.set_tuning(kernel_timing=1)
-        p64.apply_plan(plan64)  # warm-up on a throwaway state
+        p64.apply_plan(plans64[0])  # warm-up on a throwaway state
         init_state(p64.tensor)
         torch.cuda.synchronize(dev)
         ps.ps_reset_stats(p64.handle)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        p64.apply_plan(plan64)
+        for pl in plans64:
+            p64.apply_plan(pl)
         g64 = p64.overlap(p64_0)
         e1.record(stream)
         torch.cuda.synchronize(dev)
         ms64 = e0.elapsed_time(e1)
         st64 = p64.stats()
-        # complex64 on the same prefix, compared with the FP64 state
+        # complex64 on the same rotations, compared with the FP64 state
         psi.copy_from(psi0)
-        psi.apply_plan(plan32)
+        for pl in plans32:
+            psi.apply_plan(pl)
         g32 = psi.overlap(psi0)
         diff = torch.linalg.vector_norm(psi.tensor.to(torch.complex128) * psi.scale() - p64.tensor * p64.scale()).item()
-        ref = torch.linalg.vector_norm(p64.tensor).item()
+        ref = torch.linalg.vector_norm(p64.tensor * p64.scale()).item()
         tile64 = st64["kernel_ms"]["tile"] / max(st64["launches"]["tile"], 1)
-        fp64 = {"value": FP64_PREFIX / (ms64 / 1e3), "unit": UNIT, "dtype": "f64", "rotations": FP64_PREFIX,
-                "rot_per_pass": plan64.info["rotations"] / max(plan64.info["windows"], 1),
+        fp64 = {"value": nrot / (ms64 / 1e3), "unit": UNIT, "dtype": "f64", "rotations": nrot,
+                "rot_per_pass": sum(pl.info["rotations"] for pl in plans64) / max(1, sum(pl.info["windows"] for pl in plans64)),
                 "tile_avg_launch_ms": tile64,
                 "tile_achieved_gbs": 2.0 * 16.0 * (1 << N_QUBITS) / (tile64 / 1e3) / 1e9 if tile64 > 0 else None,
                 "bound": "alu (FP64 pipe)",
                 "c64_vs_fp64": {"state_rel_l2": diff / ref, "overlap_abs": abs(g32 - g64),
-                                "after_rotations": FP64_PREFIX}}
-        del p64, p64_0
+                                "overlap_rel": abs(g32 - g64) / abs(g64), "overlap_fp64": [g64.real, g64.imag],
+                                "after_rotations": nrot}}
+        del p64, p64_0, plans64, plans32
         torch.cuda.empty_cache()
 
     # ------------------------------------------------------------- end to end
@@ -396,17 +474,6 @@ def run_e2e(ps, torch, dev, segs, idx, amp, steps):
     return {"value": steps * SEG_LEN / dt, "unit": UNIT, "h2d_bytes_per_step": h2d / steps,
             "d2h_bytes_per_step": 16, "note": "wall clock; includes 2 x 8 GiB state upload, host scheduling, "
                                               "per-step rotation upload and overlap readback"}
-
-
-def cpu_baseline_leg():
-    try:
-        rate, dt = cpu_baseline_sample(CPU_SAMPLE_ROTATIONS)
-    except Exception as e:  # noqa: BLE001
-        return {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "error": str(e)}
-    return {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"first {CPU_SAMPLE_ROTATIONS} rotations of the same qDRIFT stream at n={N_QUBITS}, "
-                      f"complex128 scatter-form oracle, 1 thread ({dt:.1f} s)",
-            "host_cores_available": os.cpu_count()}
 
 
 # ---------------------------------------------------------------- batched
@@ -681,42 +748,49 @@ def run_learned(args):
 # -------------------------------------------------------------- reference
 
 def run_reference(args):
+    """The oracle as it stands, on the host cores: each step applies the next
+    REF_ROTATIONS_PER_STEP rotations of the same n = 30 qDRIFT stream on every
+    host core and reads the FP64 overlap <psi0|psi>, so the metric and unit
+    are the GPU arm's.  A single-threaded figure on the first rotations is
+    reported beside it.  Under torchrun only rank 0 runs."""
     rank, world, _ = dist_env()
     if rank != 0:
         return
     import oracle
-    from paper_2504_17881_gb300 import inputs
-    x, z, h = inputs.jw_hamiltonian(N_QUBITS, N_TERMS, seed=HAM_SEED)
-    total = args.warmup + args.steps
-    idx = oracle.qdrift_indices(h, QDRIFT_SEED, 0, total).astype(np.int64)
-    lam = 0.0
-    for v in h:
-        lam += abs(float(v))
-    tau = lam * T_TOTAL / N_SAMPLES
-    sidx, samp = inputs.determinant_state(N_QUBITS, seed=PSI0_SEED)
-    psi = np.zeros(1 << N_QUBITS, dtype=np.complex128)
-    psi[sidx.astype(np.int64)] = samp
-    tmp = np.zeros_like(psi)
-
-    def step(j):
-        oracle.apply_inplace(psi, tmp, [x[idx[j]]], [z[idx[j]]], [tau if h[idx[j]] > 0 else -tau])
-
-    for j in range(args.warmup):
-        step(j)
+    cores = host_cores()
+    threads = cores if oracle.has_openmp() else 1
+    total = (args.warmup + args.steps) * REF_ROTATIONS_PER_STEP
+    run = OracleRun(total)
+    dt1 = run.apply(0, CPU_ROTATIONS_1T, 1)
+    run.reset()
+    pos = 0
+    for _ in range(args.warmup):
+        run.apply(pos, REF_ROTATIONS_PER_STEP, cores)
+        run.overlap(cores)
+        pos += REF_ROTATIONS_PER_STEP
     t0 = time.perf_counter()
-    for j in range(args.warmup, total):
-        step(j)
+    g = 0j
+    for _ in range(args.steps):
+        run.apply(pos, REF_ROTATIONS_PER_STEP, cores)
+        g = run.overlap(cores)
+        pos += REF_ROTATIONS_PER_STEP
     dt = time.perf_counter() - t0
-    value = args.steps / dt
-    sample = (f"one rotation per step of the same qDRIFT stream at n={N_QUBITS} (complex128 scatter-form "
-              f"oracle, 1 thread); {args.steps} timed steps after {args.warmup} warm-up")
+    value = args.steps * REF_ROTATIONS_PER_STEP / dt
+    sample = (f"{REF_ROTATIONS_PER_STEP} rotations of the same qDRIFT stream at n={N_QUBITS} + the FP64 overlap per "
+              f"step (complex128 scatter-form oracle, OpenMP over {threads} threads); {args.steps} timed steps "
+              f"after {args.warmup} warm-up")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": workload_name(), "n": N_QUBITS, "terms": N_TERMS, "samples": N_SAMPLES},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "config": {"workload": workload_name(), "n": N_QUBITS, "terms": N_TERMS, "samples": N_SAMPLES,
+                   "rotations_per_step": REF_ROTATIONS_PER_STEP},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample,
+                         "single_thread": {"value": CPU_ROTATIONS_1T / dt1, "unit": UNIT, "cores": 1,
+                                           "sample": f"first {CPU_ROTATIONS_1T} rotations, 1 thread"},
+                         "host_cores_available": cores},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "overlap_last": [g.real, g.imag],
     }), flush=True)
 
 

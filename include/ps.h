@@ -135,6 +135,16 @@ void ps_destroy(ps_state *st);
 int ps_set_state(ps_state *st, const void *host_src);
 int ps_get_state(ps_state *st, void *host_dst);
 
+/* The state the handle represents, f * (stored amplitudes) with the carried
+ * scale f of ps_get_scale, written as 2^n complex128 values (16 bytes per
+ * amplitude, re/im interleaved) whatever the handle's dtype.  ps_get_state
+ * returns the stored amplitudes, which for PS_C64 differ from the
+ * represented state by up to 2^-16 relative; this call applies f in FP64 on
+ * the host copy, so a comparison with an FP64 reference needs no extra step.
+ * host_dst (caller-owned, 16 * 2^n bytes) is also the staging buffer.
+ * Synchronises the state's stream. */
+int ps_get_state_represented(ps_state *st, void *host_dst);
+
 /* dst <- src (device to device, on dst's stream); same n and dtype. */
 int ps_copy_state(ps_state *dst, const ps_state *src);
 
@@ -215,7 +225,9 @@ int ps_overlap(const ps_state *psi0, ps_state *psi, double out[2]);
  * (FP64, same fixed summation order as ps_overlap) as two doubles (re, im) to
  * the caller's device memory out_dev.  psi0_dev, psi_dev: 2^n amplitudes of
  * dtype, 16-byte aligned, on the current device.  Asynchronous on `stream`.
- * n outside [1, 40] (the range the fixed scratch serves) gives PS_ERR_ARG.
+ * n outside [1, 40] (the range the fixed scratch serves) gives PS_ERR_ARG; a
+ * current device index of 64 or more gives PS_ERR_UNSUPPORTED (the per-device
+ * address cache has 64 entries).
  * The first call on a device looks up the scratch array's device address
  * (one cudaGetSymbolAddress); make that first call before any stream
  * capture.  All calls share the one array: calls that can run at the same
@@ -299,12 +311,6 @@ int ps_partial2_stream(const ps_ham *ham, size_t L_D, double t, uint32_t r, uint
  * deterministic terms are ordered lexicographically, so strings that share
  * their upper qubits are applied together). */
 int ps_ham_sort_lexicographic(ps_ham *ham);
-/* The randomised part's samples per Trotter stage exactly as printed
- * (Methods, "Data analysis"): kappa = delta / (0.2 pi),
- * r = ceil(kappa lambda_R^2 delta^2 2^M).  The printed form grows like
- * delta^3 and looks garbled, so the drivers never use it; callers pass
- * their own sample count.  0 for negative arguments or M outside 0..62. */
-uint64_t ps_partial_sample_count(double delta, double lambda_R, int M);
 
 /* Robust-phase-estimation signal (Methods, "Data analysis"):
  *   Z_m = g(delta 2^m) = <psi0| U(delta)^(2^m) |psi0>,  m = 0..M,

@@ -22,12 +22,15 @@ _lib = None
 
 
 def build(force: bool = False) -> str:
-    """Compile ``oracle.c`` with gcc (no fused multiply-adds) into ``liboracle.so``."""
+    """Compile ``oracle.c`` with gcc (no fused multiply-adds) into ``liboracle.so``,
+    with OpenMP when the compiler has it (the pragmas are ignored otherwise)."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(
-            ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared",
-             "-o", tmp, _SRC, "-lm"])
+        base = ["gcc", "-O2", "-std=gnu11", "-ffp-contract=off", "-fcx-limited-range", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
+        try:
+            subprocess.check_call(base[:1] + ["-fopenmp"] + base[1:], stderr=subprocess.DEVNULL)
+        except subprocess.CalledProcessError:
+            subprocess.check_call(base)
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -52,17 +55,28 @@ def _load():
         "or_qdrift": (i32, [i32, vp, vp, sz, vp, vp, vp, f64, u64, u64]),
         "or_partial_split": (i32, [sz, vp, sz, vp]),
         "or_partial": (i32, [i32, vp, vp, sz, vp, vp, vp, sz, f64, u32, u64, u64]),
-        "or_partial_sample_count": (u64, [f64, f64, i32]),
         "or_trotter2": (i32, [i32, vp, vp, sz, vp, vp, vp, f64, u32]),
         "or_partial2": (i32, [i32, vp, vp, sz, vp, vp, vp, sz, f64, u32, u64, u64]),
         "or_amplitudes_sparse": (i32, [i32, sz, vp, vp, vp, vp, vp, sz, sz, vp, vp]),
     }
+    sig["or_set_threads"] = (i32, [i32])
+    sig["or_has_openmp"] = (i32, [])
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
         fn.restype = res
         fn.argtypes = args
+    lib.or_set_threads(1)
     _lib = lib
     return lib
+
+
+def set_threads(nthreads: int) -> int:
+    """Threads of the oracle's element loops (1 by default); returns the number in effect."""
+    return int(_load().or_set_threads(int(nthreads)))
+
+
+def has_openmp() -> bool:
+    return bool(_load().or_has_openmp())
 
 
 def _p(a: np.ndarray):
@@ -212,10 +226,6 @@ def partial2(psi, x, z, h, L_D: int, t: float, r: int, Ns: int, seed: int) -> np
     _check(_load().or_partial2(a.size.bit_length() - 1, _p(a), _p(tmp), x.size, _p(x), _p(z), _p(h),
                                int(L_D), float(t), int(r), int(Ns), int(seed)), "partial2")
     return a
-
-
-def partial_sample_count(delta: float, lambda_R: float, M: int) -> int:
-    return int(_load().or_partial_sample_count(float(delta), float(lambda_R), int(M)))
 
 
 def amplitudes_sparse(n: int, idx0, amp0, x, z, phi, ks) -> np.ndarray:

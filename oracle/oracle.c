@@ -10,8 +10,16 @@
  *
  * Everything is written for clarity, not speed: one loop per definition,
  * `double _Complex` amplitudes (the paper's own storage type, Methods,
- * "Mathematical model"), sequential FP64 sums, no blocking, no fusion.
+ * "Mathematical model"), FP64 sums, no blocking, no fusion.
  * Compile with -ffp-contract=off so that every product is rounded as written.
+ *
+ * Built with -fopenmp, the element loops are shared among threads by plain
+ * `omp parallel for` pragmas (or_set_threads; one thread by default).  Each
+ * element is still computed by exactly the same expression: the scatter of
+ * one rotation writes every output element once (k -> k XOR x is a
+ * bijection), so threads never touch the same element.  Only the order of
+ * the FP64 sums in or_overlap / or_norm2 depends on the thread count; with
+ * one thread they run in index order.
  *
  * Conventions fixed by the paper:
  *   - qubit q (1-based, leftmost factor of the string) is bit q-1 of the
@@ -29,17 +37,44 @@
  *
  * Parity status: every function here is pinned by the "not gpu" tests
  * (dense Kronecker products and matrix exponentials, closed forms,
- * invariants, published SplitMix64 outputs), except or_partial_sample_count,
- * which computes a formula the paper prints in apparently garbled form
- * (parity unpinned).
+ * invariants, published SplitMix64 outputs).
  */
 #include <complex.h>
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 typedef double _Complex cplx;
+
+/* ------------------------------------------------------------------ threads */
+
+/* Threads of the element loops (ignored without OpenMP).  Returns the
+ * number in effect: 1 when the library was built without OpenMP. */
+int or_set_threads(int nthreads)
+{
+#ifdef _OPENMP
+    if (nthreads < 1) nthreads = 1;
+    omp_set_num_threads(nthreads);
+    return omp_get_max_threads();
+#else
+    (void)nthreads;
+    return 1;
+#endif
+}
+
+/* 1 when built with OpenMP, else 0. */
+int or_has_openmp(void)
+{
+#ifdef _OPENMP
+    return 1;
+#else
+    return 0;
+#endif
+}
 
 /* ---------------------------------------------------------------- encoding */
 
@@ -109,9 +144,12 @@ int or_rotate(int n, cplx *psi, cplx *tmp, uint64_t x, uint64_t z, double phi)
     uint64_t N = (uint64_t)1 << n;
     if ((x | z) >> n) return -1;
     double c = cos(phi), s = sin(phi);
+#pragma omp parallel for schedule(static)
     for (uint64_t k = 0; k < N; ++k) tmp[k] = c * psi[k];
+#pragma omp parallel for schedule(static)
     for (uint64_t k = 0; k < N; ++k) tmp[k ^ x] += (I * s) * omega(x, z, k) * psi[k];
-    memcpy(psi, tmp, N * sizeof(cplx));
+#pragma omp parallel for schedule(static)
+    for (uint64_t k = 0; k < N; ++k) psi[k] = tmp[k];
     return 0;
 }
 
@@ -134,16 +172,22 @@ int or_apply(int n, cplx *psi, cplx *tmp, const uint64_t *x, const uint64_t *z,
 void or_overlap(int n, const cplx *a, const cplx *b, double out[2])
 {
     uint64_t N = (uint64_t)1 << n;
-    cplx acc = 0.0;
-    for (uint64_t k = 0; k < N; ++k) acc += conj(a[k]) * b[k];
-    out[0] = creal(acc);
-    out[1] = cimag(acc);
+    double re = 0.0, im = 0.0; /* the real and imaginary parts of the running complex sum */
+#pragma omp parallel for schedule(static) reduction(+ : re, im)
+    for (uint64_t k = 0; k < N; ++k) {
+        cplx p = conj(a[k]) * b[k];
+        re += creal(p);
+        im += cimag(p);
+    }
+    out[0] = re;
+    out[1] = im;
 }
 
 double or_norm2(int n, const cplx *a)
 {
     uint64_t N = (uint64_t)1 << n;
     double acc = 0.0;
+#pragma omp parallel for schedule(static) reduction(+ : acc)
     for (uint64_t k = 0; k < N; ++k) acc += creal(a[k]) * creal(a[k]) + cimag(a[k]) * cimag(a[k]);
     return acc;
 }
@@ -364,16 +408,6 @@ int or_partial2(int n, cplx *psi, cplx *tmp, size_t L, const uint64_t *x, const 
     return rc;
 }
 
-/* Sample count printed in Methods, "Data analysis":
- * kappa = delta / (0.2 pi), r = ceil(kappa lambda_R^2 delta^2 2^M).
- * The printed form makes r grow like delta^3, which looks garbled; it is
- * computed exactly as printed.  Parity unpinned. */
-uint64_t or_partial_sample_count(double delta, double lambda_R, int M)
-{
-    double kappa = delta / (0.2 * 3.14159265358979323846);
-    return (uint64_t)ceil(kappa * lambda_R * lambda_R * delta * delta * ldexp(1.0, M));
-}
-
 /* ------------------------------------------------- single amplitudes, any n */
 
 /* Amplitude <k| U_R ... U_1 |psi0> for a sparse initial state (nnz basis
@@ -390,18 +424,18 @@ static cplx sparse_lookup(size_t nnz, const uint64_t *idx0, const double *amp0, 
 }
 
 static cplx amp_rec(size_t level, uint64_t k, size_t nnz, const uint64_t *idx0, const double *amp0,
-                    const uint64_t *x, const uint64_t *z, const double *phi)
+                    const uint64_t *x, const uint64_t *z, const double *cs, const double *sn)
 {
     if (level == 0) return sparse_lookup(nnz, idx0, amp0, k);
     size_t j = level - 1;
-    double c = cos(phi[j]), s = sin(phi[j]);
+    double c = cs[j], s = sn[j];
     uint64_t kp = k ^ x[j];
     if (kp == k) {
-        cplx prev = amp_rec(j, k, nnz, idx0, amp0, x, z, phi);
+        cplx prev = amp_rec(j, k, nnz, idx0, amp0, x, z, cs, sn);
         return c * prev + (I * s) * omega(x[j], z[j], kp) * prev;
     }
-    return c * amp_rec(j, k, nnz, idx0, amp0, x, z, phi) +
-           (I * s) * omega(x[j], z[j], kp) * amp_rec(j, kp, nnz, idx0, amp0, x, z, phi);
+    return c * amp_rec(j, k, nnz, idx0, amp0, x, z, cs, sn) +
+           (I * s) * omega(x[j], z[j], kp) * amp_rec(j, kp, nnz, idx0, amp0, x, z, cs, sn);
 }
 
 int or_amplitudes_sparse(int n, size_t nnz, const uint64_t *idx0, const double *amp0,
@@ -412,10 +446,21 @@ int or_amplitudes_sparse(int n, size_t nnz, const uint64_t *idx0, const double *
     size_t nondiag = 0;
     for (size_t j = 0; j < R; ++j) nondiag += (x[j] != 0);
     if (nondiag > 26) return -1;
+    /* cos and sin of every angle, once (the recursion visits each level many times) */
+    double *cs = (double *)malloc((R ? R : 1) * sizeof(double));
+    double *sn = (double *)malloc((R ? R : 1) * sizeof(double));
+    if (!cs || !sn) { free(cs); free(sn); return -2; }
+    for (size_t j = 0; j < R; ++j) {
+        cs[j] = cos(phi[j]);
+        sn[j] = sin(phi[j]);
+    }
+#pragma omp parallel for schedule(dynamic, 1)
     for (size_t i = 0; i < nk; ++i) {
-        cplx a = amp_rec(R, ks[i], nnz, idx0, amp0, x, z, phi);
+        cplx a = amp_rec(R, ks[i], nnz, idx0, amp0, x, z, cs, sn);
         out[2 * i] = creal(a);
         out[2 * i + 1] = cimag(a);
     }
+    free(cs);
+    free(sn);
     return 0;
 }

@@ -89,6 +89,7 @@ _SIGS = {
     "ps_destroy": (None, [_vp]),
     "ps_set_state": (_i, [_vp, _vp]),
     "ps_get_state": (_i, [_vp, _vp]),
+    "ps_get_state_represented": (_i, [_vp, _vp]),
     "ps_copy_state": (_i, [_vp, _vp]),
     "ps_set_tuning": (_i, [_vp, ctypes.POINTER(ps_tuning)]),
     "ps_apply_rotations": (_i, [_vp, _vp, _vp, _vp, _sz]),
@@ -129,7 +130,6 @@ _SIGS = {
     "ps_partial2_length": (_u64, [_vp, _sz, _u32, _u64]),
     "ps_partial2_stream": (_i, [_vp, _sz, _d, _u32, _u64, _u64, _vp, _vp, _vp]),
     "ps_ham_sort_lexicographic": (_i, [_vp]),
-    "ps_partial_sample_count": (_u64, [_d, _d, _i]),
     "ps_rpe_signal": (_i, [_vp, _vp, _vp, _i, _sz, _d, _u32, _u64, _u64, _vp]),
     "ps_rpe_estimate": (_i, [_vp, _u32, _d, ctypes.POINTER(_d), _vp]),
     "ps_shard_plan": (_i, [_i, _i, _i, _vp, _vp, _vp, _sz, ctypes.POINTER(_sz), _vp, _vp, _vp, _vp, _vp]),
@@ -214,6 +214,10 @@ def ps_set_state(h: int, host_ptr: int):
 
 def ps_get_state(h: int, host_ptr: int):
     _check(lib.ps_get_state(ctypes.c_void_p(h), ctypes.c_void_p(host_ptr)))
+
+
+def ps_get_state_represented(h: int, host_ptr: int):
+    _check(lib.ps_get_state_represented(ctypes.c_void_p(h), ctypes.c_void_p(host_ptr)))
 
 
 def ps_copy_state(dst: int, src: int):
@@ -711,7 +715,3 @@ def ps_shard_plan(n: int, m: int, rank: int, x, z, phi):
         start = e
     return out
 
-
-def ps_partial_sample_count(delta: float, lambda_R: float, M: int) -> int:
-    """The randomised part's samples per stage as the paper prints it (opt-in; looks garbled)."""
-    return int(lib.ps_partial_sample_count(delta, lambda_R, M))

@@ -351,6 +351,32 @@ int ps_get_state(ps_state *st, void *host_dst) {
     return PS_OK;
 }
 
+int ps_get_state_represented(ps_state *st, void *host_dst) {
+    if (int rc = check_state(st)) return rc;
+    if (!host_dst) return fail(PS_ERR_ARG, "null host buffer");
+    DeviceGuard g(st->device);
+    // the stored amplitudes land in the front of the buffer; complex64 ones are
+    // widened in place from the last element down (element i's 16 output bytes
+    // start at or above byte 16 i, so no unread input is overwritten)
+    PS_CUDA(cudaMemcpyAsync(host_dst, st->psi, state_bytes(st), cudaMemcpyDeviceToHost, st->stream),
+            "ps_get_state_represented");
+    PS_CUDA(cudaStreamSynchronize(st->stream), "cudaStreamSynchronize");
+    const uint64_t N = 1ull << st->n;
+    const double f = st->pending;
+    double *out = static_cast<double *>(host_dst);
+    if (st->dtype == PS_C64) {
+        const float *in = static_cast<const float *>(host_dst);
+        for (uint64_t i = N; i-- > 0;) {
+            const double re = (double)in[2 * i], im = (double)in[2 * i + 1];
+            out[2 * i] = f * re;
+            out[2 * i + 1] = f * im;
+        }
+    } else if (f != 1.0) {
+        for (uint64_t i = 0; i < 2 * N; ++i) out[i] *= f;
+    }
+    return PS_OK;
+}
+
 int ps_copy_state(ps_state *dst, const ps_state *src) {
     if (int rc = check_state(dst)) return rc;
     if (int rc = check_state(src)) return rc;
@@ -670,11 +696,6 @@ int ps_partial2_stream(const ps_ham *ham, size_t L_D, double t, uint32_t r, uint
     std::copy(s.z.begin(), s.z.end(), z_out);
     std::copy(s.phi.begin(), s.phi.end(), phi_out);
     return PS_OK;
-}
-
-uint64_t ps_partial_sample_count(double delta, double lambda_R, int M) {
-    if (!(delta >= 0.0) || !(lambda_R >= 0.0) || M < 0 || M > 62) return 0;
-    return printed_sample_count(delta, lambda_R, M);
 }
 
 int ps_ham_sort_lexicographic(ps_ham *ham) {

@@ -40,9 +40,13 @@ SymbolCache &cache() {
 int partials_on_current_device(double **out, std::string *err) {
     int dev = -1;
     cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess || dev < 0 || dev >= 64) {
+    if (e != cudaSuccess) {
         *err = std::string("cudaGetDevice: ") + cudaGetErrorString(e);
         return PS_ERR_CUDA;
+    }
+    if (dev < 0 || dev >= 64) {
+        *err = "device index " + std::to_string(dev) + " is outside the 64-entry scratch address cache";
+        return PS_ERR_UNSUPPORTED;
     }
     SymbolCache &c = cache();
     std::lock_guard<std::mutex> lock(c.mu);

@@ -276,15 +276,6 @@ void product_steps(const Ham &H, int order, size_t L_D, double delta, uint64_t N
     }
 }
 
-// The randomised part's samples per Trotter stage as printed (Methods, "Data
-// analysis"): kappa = delta / (0.2 pi), r = ceil(kappa lambda_R^2 delta^2 2^M).
-// The printed form makes r grow like delta^3, which looks garbled; it is
-// computed as printed and offered as an opt-in helper only.
-uint64_t printed_sample_count(double delta, double lambda_R, int M) {
-    const double kappa = delta / (0.2 * 3.14159265358979323846);
-    return (uint64_t)std::ceil(kappa * lambda_R * lambda_R * delta * delta * std::ldexp(1.0, M));
-}
-
 // Term order by the Pauli string read from qubit n down to qubit 1, letters
 // I < X < Y < Z, ties in input order (Methods: deterministic terms are
 // ordered lexicographically so that strings sharing their upper qubits are

@@ -34,7 +34,6 @@ void trotter2_stream(const Ham &H, double t, uint32_t r, Stream &out);
 uint64_t partial2_length(const Ham &H, size_t L_D, uint32_t r, uint64_t Ns);
 void partial2_stream(const Ham &H, size_t L_D, double t, uint32_t r, uint64_t Ns, uint64_t seed, Stream &out);
 void lexicographic_sort(Ham &H);
-uint64_t printed_sample_count(double delta, double lambda_R, int M);
 void product_steps(const Ham &H, int order, size_t L_D, double delta, uint64_t Ns, uint64_t seed, uint64_t step0,
                    uint64_t nsteps, Stream &out);
 

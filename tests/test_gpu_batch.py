@@ -55,7 +55,7 @@ def single_run(r, dtype):
     st = ps.StateVector(r["n"], dtype=TDT[dtype])
     st.load(r["host0"])
     st.apply_rotations(r["x"], r["z"], r["phi"])
-    return st.to_numpy().astype(np.complex128) * st.scale()
+    return st.to_numpy()
 
 
 @pytest.mark.parametrize("dtype", [ps.PS_C128, ps.PS_C64])

@@ -368,9 +368,3 @@ def test_split_optimizer_matches_enumeration_with_the_oracle_bound():
     assert ps.ps_partial_optimize_split(H.handle, 1e-3, 1e-6, 1e6)[0] == len(h)
     assert lam > 0
 
-
-def test_printed_sample_count_equals_the_oracle_formula():
-    # both compute the printed formula (parity unpinned: the formula itself looks garbled)
-    for delta, lam_r, M in ((0.1, 2.0, 3), (0.5, 0.7, 6), (0.05, 5.0, 10), (0.0, 1.0, 2)):
-        assert ps.ps_partial_sample_count(delta, lam_r, M) == oracle.partial_sample_count(delta, lam_r, M)
-    assert ps.ps_partial_sample_count(-1.0, 1.0, 2) == 0

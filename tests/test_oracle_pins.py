@@ -437,3 +437,27 @@ def test_lexicographic_order_hand_example():
     xz = [oracle.pauli_from_string(s) for s in terms]
     order = oracle.lexicographic_order(2, [a for a, _ in xz], [b for _, b in xz])
     assert order == [1, 2, 3, 0]
+
+
+def test_threaded_oracle_gives_the_same_rotations():
+    """The OpenMP pragmas only share the element loops among threads: a
+    rotation writes every output element once, so the state is bitwise the
+    same for any thread count; only the order of the overlap and norm sums
+    changes (a few ulps)."""
+    n = 14
+    psi0 = inputs.gaussian_state(n, 51)
+    x, z, phi = inputs.random_rotations(n, 40, seed=52)
+    one = oracle.apply(psi0, x, z, phi)
+    g1, n1 = oracle.overlap(psi0, one), oracle.norm2(one)
+    a1 = oracle.amplitudes_sparse(n, [5, 77], [0.6, 0.8j], x[:12], z[:12], phi[:12], [5, 77, 5 ^ int(x[0])])
+    try:
+        used = oracle.set_threads(4)
+        many = oracle.apply(psi0, x, z, phi)
+        g4, n4 = oracle.overlap(psi0, many), oracle.norm2(many)
+        a4 = oracle.amplitudes_sparse(n, [5, 77], [0.6, 0.8j], x[:12], z[:12], phi[:12], [5, 77, 5 ^ int(x[0])])
+    finally:
+        oracle.set_threads(1)
+    assert used == (4 if oracle.has_openmp() else 1)
+    assert np.array_equal(one, many)
+    assert np.array_equal(a1, a4)
+    assert abs(g1 - g4) < 1e-14 and abs(n1 - n4) < 1e-14

@@ -130,7 +130,7 @@ def test_ranks_emulated_on_one_gpu_with_libps(dtype, tol):
         k = int(np.log2(st.size))
         sv = ps.StateVector(k, tensor=torch.as_tensor(st).to(dtype).cuda())
         sv.apply_rotations(a, b, c)
-        return sv.to_numpy().astype(np.complex128) * sv.scale()
+        return sv.to_numpy()
 
     got = emulate(n, m, psi, xs, zs, ph, apply)
     ref = oracle.apply(psi, xs, zs, ph)
