@@ -71,7 +71,7 @@ def parse():
     ap.add_argument("--fp64-rotations", type=int, default=SEG_LEN,
                     help="rotations of the stream run in complex128 and complex64 for the error report "
                          "(default one segment; 100000 for the whole run)")
-    ap.add_argument("--workload", choices=["qdrift30", "batched", "learned"], default="qdrift30",
+    ap.add_argument("--workload", choices=["qdrift30", "batched", "learned", "trotter26"], default="qdrift30",
                     help="batched: 512 independent qDRIFT / partially randomised runs, n 14..22, in one "
                          "persistent launch (reported on its own JSON line)")
     ap.add_argument("--batch-runs", type=int, default=BATCH_RUNS)
@@ -745,6 +745,100 @@ def run_learned(args):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------- Trotter n=26
+
+T26_N = 26
+T26_TERMS = 2000
+T26_HAM_SEED = 2
+T26_PSI0_SEED = 21
+T26_TIMES = [0.1 * 2.0 ** (j / 3.0) for j in range(16)]
+T26_STEPS = [1, 2, 4, 8, 16, 32, 64]
+
+
+def run_trotter26(args):
+    """The n = 26 first-order Trotter sweep: a 2000-term JW-like Hamiltonian
+    (one-norm 3.5), 16 times 0.1 * 2^(j/3) (0.1 .. 3.2), r in {1, 2, ..., 64};
+    every (t, r) evolved from the 8-determinant state and closed with the FP64
+    overlap, once in complex64 and once in complex128.  Reported: each pair's
+    overlaps and their difference, the Trotter error against r = 64 (complex128),
+    rotations/s of both dtypes (whole sweep, host scheduling included) and the
+    tile kernel's roofline."""
+    import torch
+    import paper_2504_17881_gb300 as ps
+    from paper_2504_17881_gb300 import inputs
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    n = T26_N
+    x, z, h = inputs.jw_hamiltonian(n, T26_TERMS, seed=T26_HAM_SEED)
+    H = ps.Hamiltonian(n, x, z, h)
+    idx, amp = inputs.determinant_state(n, seed=T26_PSI0_SEED)
+    peak, peak_kind = hbm_peak()
+    out = {}
+    per_dtype = {}
+    for name, tdt, dt in (("c64", torch.complex64, ps.PS_C64), ("c128", torch.complex128, ps.PS_C128)):
+        st0 = ps.StateVector(n, dtype=tdt, device=dev)
+        st0.tensor.zero_()
+        st0.tensor[torch.as_tensor(idx.astype(np.int64), device=dev)] = torch.as_tensor(amp, device=dev).to(tdt)
+        work = ps.StateVector(n, dtype=tdt, device=dev)
+        work.set_tuning(kernel_timing=1)
+        work.copy_from(st0)
+        work.evolve_trotter(H, T26_TIMES[0], 1)  # warm-up
+        work.overlap(st0)
+        torch.cuda.synchronize(dev)
+        ps.ps_reset_stats(work.handle)
+        clocks = ClockSampler(0) if name == "c64" else None
+        if clocks:
+            clocks.start()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        rot = 0
+        for t in T26_TIMES:
+            for r in T26_STEPS:
+                work.copy_from(st0)
+                work.evolve_trotter(H, t, r)
+                out.setdefault((t, r), {})[name] = work.overlap(st0)
+                rot += r * T26_TERMS
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        clk = clocks.stop() if clocks else None
+        ms = e0.elapsed_time(e1)
+        stats = work.stats()
+        tile_ms = stats["kernel_ms"]["tile"] / max(stats["launches"]["tile"], 1)
+        S = 8 if name == "c64" else 16
+        per_dtype[name] = {"value": rot / (ms / 1e3), "unit": UNIT, "rotations": rot, "seconds": ms / 1e3,
+                           "passes": stats["passes"], "rot_per_pass": rot / max(stats["passes"], 1),
+                           "tile_avg_launch_ms": tile_ms,
+                           "tile_achieved_gbs": 2.0 * S * (1 << n) / (tile_ms / 1e3) / 1e9 if tile_ms > 0 else None,
+                           "gpu_launches": sum(stats["launches"].values()), "clocks": clk}
+        del work, st0
+        torch.cuda.empty_cache()
+    rows = []
+    for t in T26_TIMES:
+        ref = out[(t, T26_STEPS[-1])]["c128"]
+        for r in T26_STEPS:
+            g32, g64 = out[(t, r)]["c64"], out[(t, r)]["c128"]
+            rows.append({"t": t, "r": r, "g_c64": [g32.real, g32.imag], "g_c128": [g64.real, g64.imag],
+                         "c64_vs_c128_abs": abs(g32 - g64), "trotter_err_vs_r64_c128": abs(g64 - ref)})
+    c64 = per_dtype["c64"]
+    ach = c64["tile_achieved_gbs"]
+    line = {
+        "metric": f"first-order Trotter sweep at n={n}: rotations/s, complex64 vs FP64", "value": c64["value"],
+        "unit": UNIT, "n_gpus": 1, "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"trotter n={n}: JW-like H with {T26_TERMS} terms (lambda 3.5, seed {T26_HAM_SEED}), "
+                               f"16 times 0.1*2^(j/3), r in {T26_STEPS}, 8-determinant initial state; every (t, r) "
+                               f"from psi0 with an FP64 overlap", "pairs": len(rows),
+                   "l2": f"inputs larger than L2 ({8 << n >> 20} MiB c64 state), no flush"},
+        "roofline": {"bound": "hbm", "kernel": "k_tile<float,3,4>", "achieved": ach, "peak": peak, "unit": "GB/s",
+                     "frac": ach / peak if ach else None, "traffic": None,
+                     "peak_source": f"{peak_kind} copy bandwidth"},
+        "c64": c64, "c128": per_dtype["c128"],
+        "max_c64_vs_c128_abs": max(rw["c64_vs_c128_abs"] for rw in rows), "rows": rows,
+    }
+    print(json.dumps(line), flush=True)
+
+
 # -------------------------------------------------------------- reference
 
 def run_reference(args):
@@ -804,6 +898,8 @@ def main():
         run_batched(args)
     elif args.workload == "learned":
         run_learned(args)
+    elif args.workload == "trotter26":
+        run_trotter26(args)
     else:
         run_ours(args)
 
