@@ -81,6 +81,10 @@ typedef struct ps_tuning {
                           default is capped to it).  Fewer threads give each thread more
                           register batches per round, spreading its fixed per-round work over
                           more amplitudes. */
+    int test_extra_tx; /* test hook, 0 in normal use: bytes (0..4096) that a tile pass staged
+                          by bulk copies waits for beyond its tile.  They never arrive, so the
+                          pass's bounded wait runs out (about 1 s), the pass stores nothing and
+                          the next synchronising call returns PS_ERR_TIMEOUT. */
 } ps_tuning;
 
 /* Counters of a state handle since creation or the last ps_reset_stats. */
@@ -495,6 +499,34 @@ int ps_batch_describe(int dtype, const ps_run_desc *runs, size_t nruns, const ps
  * (Methods, "Data analysis").  Host only, O(L_D^2). */
 int ps_ham_trotter_bound(const ps_ham *ham, size_t L_D, double *out);
 
+/* The step count the analytic bound gives for first-order Trotter (every
+ * term deterministic): the paper's error model eps = C delta^2 with
+ * delta = t / r (Methods, "Hamiltonian simulation"), so
+ * r = max(1, ceil(t sqrt(C / eps))), C = ps_ham_trotter_bound(ham, L).
+ * PS_ERR_ARG for t or eps not positive; PS_ERR_UNSUPPORTED when r would
+ * exceed 2^32 - 1.  Host only. */
+int ps_ham_bound_steps(const ps_ham *ham, double t, double eps, uint32_t *r_out);
+
+/* Three-point Richardson extrapolation to r -> infinity of first-order
+ * product-formula overlaps g_r = g + a / r + b / r^2 + O(r^-3) (Eq. 3 has a
+ * first-order error): out = (8 g_4R - 6 g_2R + g_R) / 3 from runs at R, 2R,
+ * 4R.  Complex values as (re, im).  Host only. */
+int ps_richardson3(const double g_R[2], const double g_2R[2], const double g_4R[2], double out[2]);
+
+/* Training labels of the learned step choice: for each of `count` overlaps
+ * g (re, im pairs), eps_out[i] = |g_i - g_lim| and
+ * log_eps_out[i] = log(max(eps_out[i], eps_floor)) (eps_floor > 0).
+ * Host only. */
+int ps_trotter_error_labels(const double *g, size_t count, const double g_lim[2], double eps_floor, double *eps_out,
+                            float *log_eps_out);
+
+/* The pick margin: the `quantile` (0..1) of the held-out residuals
+ * y[i] - pred[i] (log error minus prediction, in FP64), at least 0, so that
+ * prediction + margin bounds the error in about that fraction of cases.
+ * The quantile interpolates linearly between the sorted residuals at
+ * position quantile * (count - 1).  Host only. */
+int ps_mlp_margin(const float *y, const float *pred, size_t count, double quantile, double *margin_out);
+
 /* The leading coefficient K of the first-order Trotter error of the overlap
  * for the sparse initial state psi = sum_i amp_i |idx_i> (ndet distinct
  * basis states; amp holds re, im pairs):
@@ -583,6 +615,11 @@ int ps_mlp_predict(ps_mlp *m, const float *x_dev, size_t rows, float *y_dev);
  * Synchronous. */
 int ps_mlp_pick_r(ps_mlp *m, ps_ham *ham, const uint64_t *idx, const double *amp, size_t ndet, double t, double eps,
                   double margin, uint32_t r_max, uint32_t *r_out, float *pred_out);
+/* The ensemble's prediction for `rows` device feature rows: the mean, in
+ * member order (FP64 sum, rounded once to FP32), of every member's
+ * predicted log error, written to host memory y_host.  Synchronous. */
+int ps_mlp_predict_ensemble(ps_mlp *const *nets, int count, const float *x_dev, size_t rows, float *y_host);
+
 /* The same for an ensemble of `count` (1..64) networks on one device: the
  * prediction is the mean of the members' predicted log errors. */
 int ps_mlp_pick_r_ensemble(ps_mlp *const *nets, int count, ps_ham *ham, const uint64_t *idx, const double *amp,

@@ -15,6 +15,11 @@ Plain numpy / Python, FP64, written from the definitions:
     (twelve numbers).
   * A tanh multilayer perceptron with a linear scalar output, its mean-squared
     loss, the gradient by backpropagation, and one Adam step (Kingma & Ba).
+  * The training labels: the r -> infinity limit of first-order overlaps
+    g_r = g + a/r + b/r^2 from three runs (the 3x3 linear system solved
+    as written), eps = |g_r - g|, log eps with a floor; the pick margin (a
+    quantile of held-out residuals, numpy's); the bound's step count from
+    the paper's error model eps = C (t/r)^2.
 Only ``tests/`` may import this module.  It shares no code with the CUDA
 library.
 """
@@ -217,3 +222,32 @@ def adam_step(p, g, m, v, step: int, lr: float, beta1: float = 0.9, beta2: float
     mhat = m / (1.0 - beta1 ** step)
     vhat = v / (1.0 - beta2 ** step)
     return p - lr * mhat / (np.sqrt(vhat) + eps), m, v
+
+
+# ------------------------------------------------ labels, margin, bound steps
+
+def richardson3(g_R: complex, g_2R: complex, g_4R: complex, R: float = 1.0) -> complex:
+    """g from g_r = g + a/r + b/r^2 at r = R, 2R, 4R: the linear system in
+    (g, a, b) solved as written (the result does not depend on R)."""
+    rs = np.array([R, 2.0 * R, 4.0 * R])
+    A = np.stack([np.ones(3), 1.0 / rs, 1.0 / rs ** 2], axis=1).astype(np.complex128)
+    sol = np.linalg.solve(A, np.array([g_R, g_2R, g_4R], dtype=np.complex128))
+    return complex(sol[0])
+
+
+def error_labels(g, g_lim: complex, eps_floor: float):
+    """eps_i = |g_i - g_lim| and log(max(eps_i, eps_floor))."""
+    eps = np.array([abs(complex(v) - complex(g_lim)) for v in g])
+    return eps, np.log(np.maximum(eps, eps_floor))
+
+
+def margin(y, pred, quantile: float) -> float:
+    """The quantile of the residuals y - pred (numpy's default), at least 0."""
+    resid = np.asarray(y, np.float64) - np.asarray(pred, np.float64)
+    return max(0.0, float(np.quantile(resid, quantile)))
+
+
+def bound_steps(n: int, x, z, h, t: float, eps: float) -> int:
+    """r with C (t/r)^2 = eps rounded up, C the bound with every term deterministic."""
+    C = trotter_bound(n, x, z, h)
+    return max(1, math.ceil(t * math.sqrt(C / eps)))

@@ -25,7 +25,8 @@ from ._lib import (PS_C64, PS_C128, PS_ERR_ARG, PS_ERR_TIMEOUT, PsError, ps_abi_
                    ps_mlp_adam_step, ps_mlp_train, ps_mlp_predict, ps_mlp_pick_r,
                    ps_mlp_pick_r_ensemble, ps_evolve_trotter2, ps_evolve_partial2, ps_trotter2_length,
                    ps_trotter2_stream, ps_partial2_length, ps_partial2_stream, ps_ham_sort_lexicographic,
-                   ps_rpe_signal, ps_rpe_estimate, ps_partial_optimize_split, ps_shard_plan)
+                   ps_rpe_signal, ps_rpe_estimate, ps_partial_optimize_split, ps_shard_plan, ps_richardson3,
+                   ps_ham_bound_steps, ps_trotter_error_labels, ps_mlp_margin, ps_mlp_predict_ensemble)
 
 __all__ = [n for n in dir(_lib) if n.startswith("ps_")] + ["StateVector", "Hamiltonian", "Plan", "Batch",
                                                               "PsError", "PS_C64", "PS_C128"]

@@ -30,7 +30,7 @@ class PsError(RuntimeError):
 class ps_tuning(ctypes.Structure):
     _fields_ = [("tile_bits", ctypes.c_int), ("group_bits", ctypes.c_int), ("max_window", ctypes.c_int),
                 ("pair_single", ctypes.c_int), ("kernel_timing", ctypes.c_int), ("reg_groups", ctypes.c_int),
-                ("seg_bits", ctypes.c_int), ("tile_threads", ctypes.c_int)]
+                ("seg_bits", ctypes.c_int), ("tile_threads", ctypes.c_int), ("test_extra_tx", ctypes.c_int)]
 
 
 class ps_stats(ctypes.Structure):
@@ -135,6 +135,10 @@ _SIGS = {
     "ps_shard_plan": (_i, [_i, _i, _i, _vp, _vp, _vp, _sz, ctypes.POINTER(_sz), _vp, _vp, _vp, _vp, _vp]),
     "ps_partial_optimize_split": (_i, [_vp, _d, _d, _d, ctypes.POINTER(_sz), ctypes.POINTER(_d), ctypes.POINTER(_d)]),
     "ps_ham_trotter_bound": (_i, [_vp, _sz, ctypes.POINTER(_d)]),
+    "ps_ham_bound_steps": (_i, [_vp, _d, _d, ctypes.POINTER(ctypes.c_uint32)]),
+    "ps_richardson3": (_i, [_vp, _vp, _vp, _vp]),
+    "ps_trotter_error_labels": (_i, [_vp, _sz, _vp, _d, _vp, _vp]),
+    "ps_mlp_margin": (_i, [_vp, _vp, _sz, _d, ctypes.POINTER(_d)]),
     "ps_ham_features": (_i, [_vp, _vp, _vp, _sz, _d, _u32, _vp]),
     "ps_ham_error_coefficient": (_i, [_vp, _vp, _vp, _sz, _vp]),
     "ps_trotter_stream": (_i, [_vp, _d, _u32, _vp, _vp, _vp]),
@@ -154,6 +158,7 @@ _SIGS = {
     "ps_mlp_predict": (_i, [_vp, _vp, _sz, _vp]),
     "ps_mlp_pick_r": (_i, [_vp, _vp, _vp, _vp, _sz, _d, _d, _d, _u32, ctypes.POINTER(_u32), _vp]),
     "ps_mlp_pick_r_ensemble": (_i, [_vp, _i, _vp, _vp, _vp, _sz, _d, _d, _d, _u32, ctypes.POINTER(_u32), _vp]),
+    "ps_mlp_predict_ensemble": (_i, [_vp, _i, _vp, _sz, _vp]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _fn = getattr(lib, _name)
@@ -474,6 +479,44 @@ def ps_ham_trotter_bound(ham: int, L_D: int) -> float:
     return out.value
 
 
+def ps_ham_bound_steps(ham: int, t: float, eps: float) -> int:
+    out = ctypes.c_uint32()
+    _check(lib.ps_ham_bound_steps(ctypes.c_void_p(ham), float(t), float(eps), ctypes.byref(out)))
+    return int(out.value)
+
+
+def _c2(g) -> np.ndarray:
+    return np.array([complex(g).real, complex(g).imag], dtype=np.float64)
+
+
+def ps_richardson3(g_R: complex, g_2R: complex, g_4R: complex) -> complex:
+    a, b, c = _c2(g_R), _c2(g_2R), _c2(g_4R)
+    out = np.zeros(2)
+    _check(lib.ps_richardson3(_ptr(a), _ptr(b), _ptr(c), _ptr(out)))
+    return complex(out[0], out[1])
+
+
+def ps_trotter_error_labels(g, g_lim: complex, eps_floor: float):
+    """(eps, log eps as float32) of overlaps g against the limit g_lim."""
+    gg = np.ascontiguousarray(np.asarray(g, dtype=np.complex128)).view(np.float64)
+    n = gg.size // 2
+    lim = _c2(g_lim)
+    eps = np.zeros(n)
+    lg = np.zeros(n, np.float32)
+    _check(lib.ps_trotter_error_labels(_ptr(gg), n, _ptr(lim), float(eps_floor), _ptr(eps), _ptr(lg)))
+    return eps, lg
+
+
+def ps_mlp_margin(y, pred, quantile: float) -> float:
+    y = np.ascontiguousarray(np.asarray(y, np.float32))
+    p = np.ascontiguousarray(np.asarray(pred, np.float32))
+    if y.size != p.size:
+        raise ValueError("y and pred differ in length")
+    out = _d()
+    _check(lib.ps_mlp_margin(_ptr(y), _ptr(p), y.size, float(quantile), ctypes.byref(out)))
+    return out.value
+
+
 def _sparse(idx, amp):
     idx = _u64a(idx)
     a = np.asarray(amp, dtype=np.complex128)
@@ -607,6 +650,14 @@ def ps_mlp_pick_r(m: int, ham: int, idx, amp, t: float, eps: float, margin: floa
     if rc not in (PS_OK, PS_ERR_UNSUPPORTED):
         _check(rc)
     return int(r.value), pred
+
+
+def ps_mlp_predict_ensemble(nets, x_dev_ptr: int, rows: int) -> np.ndarray:
+    """Mean of the members' predictions for `rows` device feature rows (host float32)."""
+    arr = (ctypes.c_void_p * len(nets))(*nets)
+    out = np.zeros(rows, dtype=np.float32)
+    _check(lib.ps_mlp_predict_ensemble(arr, len(nets), ctypes.c_void_p(x_dev_ptr), rows, _ptr(out)))
+    return out
 
 
 def ps_mlp_pick_r_ensemble(nets, ham: int, idx, amp, t: float, eps: float, margin: float, r_max: int):

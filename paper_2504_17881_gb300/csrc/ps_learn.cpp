@@ -258,6 +258,55 @@ int ps_ham_trotter_bound(const ps_ham *ham, size_t L_D, double *out) {
     return PS_OK;
 }
 
+int ps_ham_bound_steps(const ps_ham *ham, double t, double eps, uint32_t *r_out) {
+    if (!ham || !r_out) return lfail(PS_ERR_ARG, "null argument");
+    if (!(t > 0.0) || !(eps > 0.0) || !std::isfinite(t) || !std::isfinite(eps))
+        return lfail(PS_ERR_ARG, "t and eps must be positive and finite");
+    const double C = trotter_bound(ham->H, ham->H.h.size());
+    const double r = std::ceil(t * std::sqrt(C / eps));
+    if (!(r < 4294967296.0)) return lfail(PS_ERR_UNSUPPORTED, "the bound's step count exceeds 2^32 - 1");
+    *r_out = r < 1.0 ? 1u : (uint32_t)r;
+    return PS_OK;
+}
+
+int ps_richardson3(const double g_R[2], const double g_2R[2], const double g_4R[2], double out[2]) {
+    if (!g_R || !g_2R || !g_4R || !out) return lfail(PS_ERR_ARG, "null argument");
+    // g_r = g + a / r + b / r^2: eliminate a and b from r = R, 2R, 4R
+    for (int k = 0; k < 2; ++k) out[k] = (8.0 * g_4R[k] - 6.0 * g_2R[k] + g_R[k]) / 3.0;
+    return PS_OK;
+}
+
+int ps_trotter_error_labels(const double *g, size_t count, const double g_lim[2], double eps_floor, double *eps_out,
+                            float *log_eps_out) {
+    if (count && (!g || !eps_out || !log_eps_out)) return lfail(PS_ERR_ARG, "null array");
+    if (!g_lim) return lfail(PS_ERR_ARG, "null limit");
+    if (!(eps_floor > 0.0)) return lfail(PS_ERR_ARG, "eps_floor must be positive");
+    for (size_t i = 0; i < count; ++i) {
+        const double e = std::hypot(g[2 * i] - g_lim[0], g[2 * i + 1] - g_lim[1]);
+        eps_out[i] = e;
+        log_eps_out[i] = (float)std::log(std::max(e, eps_floor));
+    }
+    return PS_OK;
+}
+
+int ps_mlp_margin(const float *y, const float *pred, size_t count, double quantile, double *margin_out) {
+    if (!margin_out || (count && (!y || !pred))) return lfail(PS_ERR_ARG, "null argument");
+    if (count == 0) return lfail(PS_ERR_ARG, "no held-out rows");
+    if (!(quantile >= 0.0 && quantile <= 1.0)) return lfail(PS_ERR_ARG, "quantile must be in [0, 1]");
+    std::vector<double> res(count);
+    for (size_t i = 0; i < count; ++i) res[i] = (double)y[i] - (double)pred[i];
+    std::sort(res.begin(), res.end());
+    // order statistic at position q (n - 1), linear between neighbours
+    const double pos = quantile * (double)(count - 1);
+    const size_t lo = (size_t)std::floor(pos);
+    const size_t hi = std::min(lo + 1, count - 1);
+    const double f = pos - (double)lo;
+    const double d = res[hi] - res[lo];
+    const double q = f >= 0.5 ? res[hi] - d * (1.0 - f) : res[lo] + d * f;
+    *margin_out = std::max(0.0, q);
+    return PS_OK;
+}
+
 int ps_ham_features(ps_ham *ham, const uint64_t *idx, const double *amp, size_t ndet, double t, uint32_t r,
                     float *out) {
     return ham_query_features(ham, idx, amp, ndet, t, r, out);

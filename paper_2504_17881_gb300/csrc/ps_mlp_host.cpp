@@ -388,6 +388,38 @@ int ps_mlp_predict(ps_mlp *m, const float *x_dev, size_t rows, float *y_dev) {
     return e ? cuda_mfail((cudaError_t)e, "MLP inference kernels") : PS_OK;
 }
 
+int ps_mlp_predict_ensemble(ps_mlp *const *nets, int count, const float *x_dev, size_t rows, float *y_host) {
+    if (!nets || count < 1 || count > 64 || !x_dev || !y_host) return mfail(PS_ERR_ARG, "null argument or bad count");
+    for (int k = 0; k < count; ++k) {
+        if (!nets[k]) return mfail(PS_ERR_ARG, "null network");
+        if (nets[k]->n_in != nets[0]->n_in || nets[k]->device != nets[0]->device)
+            return mfail(PS_ERR_ARG, "members differ in inputs or device");
+    }
+    if (int rc = check_rows(rows)) return rc;
+    Guard g(nets[0]->device);
+    float *dy = nullptr;
+    cudaError_t ce = cudaMalloc((void **)&dy, sizeof(float) * (size_t)count * rows);
+    if (ce != cudaSuccess) return cuda_mfail(ce, "ensemble buffers");
+    std::vector<float> all((size_t)count * rows);
+    int rc = PS_OK;
+    for (int k = 0; k < count && rc == PS_OK && ce == cudaSuccess; ++k) {
+        rc = ps_mlp_predict(nets[k], x_dev, rows, dy + (size_t)k * rows);
+        if (rc == PS_OK) ce = cudaStreamSynchronize(nets[k]->stream);
+    }
+    if (rc == PS_OK && ce == cudaSuccess)
+        ce = cudaMemcpy(all.data(), dy, sizeof(float) * all.size(), cudaMemcpyDeviceToHost);
+    cudaFree(dy);
+    if (rc) return rc;
+    if (ce != cudaSuccess) return cuda_mfail(ce, "ensemble transfer");
+    // the mean of the members' log errors, in member order (as in ps_mlp_pick_r_ensemble)
+    for (size_t i = 0; i < rows; ++i) {
+        double s = 0.0;
+        for (int k = 0; k < count; ++k) s += all[(size_t)k * rows + i];
+        y_host[i] = (float)(s / count);
+    }
+    return PS_OK;
+}
+
 int ps_mlp_pick_r_ensemble(ps_mlp *const *nets, int count, ps_ham *ham, const uint64_t *idx, const double *amp,
                            size_t ndet, double t, double eps, double margin, uint32_t r_max, uint32_t *r_out,
                            float *pred_out) {

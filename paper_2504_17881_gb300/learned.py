@@ -22,8 +22,6 @@ arranges the calls.
 """
 from __future__ import annotations
 
-import math
-
 import numpy as np
 
 from . import PS_MLP_FEATURES, Batch, Hamiltonian, StateVector, _lib, ps_trotter_sweep
@@ -35,8 +33,8 @@ EPS_FLOOR = 1e-12
 
 
 def richardson3(g32: complex, g64: complex, g128: complex) -> complex:
-    """The r -> infinity limit of g_r = g + a/r + b/r^2 from r = R, 2R, 4R."""
-    return (8.0 * g128 - 6.0 * g64 + g32) / 3.0
+    """The r -> infinity limit of g_r = g + a/r + b/r^2 from r = R, 2R, 4R (ps_richardson3)."""
+    return _lib.ps_richardson3(g32, g64, g128)
 
 
 def initial_state(n: int, seed: int, dtype, device, min_distance: int = 0, ndet: int = 8):
@@ -150,11 +148,11 @@ def training_rows(problems, times=TIMES16, r_values=R_VALUES, dtype=None, cfg=No
     for pi, p in enumerate(problems):
         for ti, t in enumerate(times):
             g_lim = richardson3(g[(pi, ti, 32)], g[(pi, ti, 64)], g[(pi, ti, R_EXTRA)])
-            for r in r_values:
-                eps = abs(g[(pi, ti, r)] - g_lim)
+            eps, log_eps = _lib.ps_trotter_error_labels([g[(pi, ti, r)] for r in r_values], g_lim, EPS_FLOOR)
+            for k, r in enumerate(r_values):
                 X.append(p.features(t, r))
-                y.append(math.log(max(eps, EPS_FLOOR)))
-                info.append((pi, ti, r, eps))
+                y.append(log_eps[k])
+                info.append((pi, ti, r, float(eps[k])))
     return np.asarray(X, np.float32), np.asarray(y, np.float32), info
 
 
@@ -207,8 +205,7 @@ class StepPredictor:
         """Margin for pick_r: the given quantile of the held-out residuals
         log eps - prediction (at least 0), so that the prediction plus the
         margin bounds the error in about that fraction of cases."""
-        resid = np.asarray(y_val, np.float64) - self.predict(X_val)
-        self.margin = max(0.0, float(np.quantile(resid, quantile)))
+        self.margin = _lib.ps_mlp_margin(y_val, self.predict(X_val), quantile)
         return self.margin
 
     def predict(self, X) -> np.ndarray:
@@ -250,11 +247,13 @@ class StepEnsemble:
                 for k, mb in enumerate(self.members)]
 
     def predict(self, X) -> np.ndarray:
-        return np.mean([mb.predict(X) for mb in self.members], axis=0)
+        import torch
+        X = np.ascontiguousarray(np.asarray(X, np.float32))
+        xd = torch.as_tensor(X).cuda()
+        return _lib.ps_mlp_predict_ensemble([mb.handle for mb in self.members], xd.data_ptr(), len(X))
 
     def calibrate_margin(self, X_val, y_val, quantile: float = 0.8) -> float:
-        resid = np.asarray(y_val, np.float64) - self.predict(X_val)
-        self.margin = max(0.0, float(np.quantile(resid, quantile)))
+        self.margin = _lib.ps_mlp_margin(y_val, self.predict(X_val), quantile)
         return self.margin
 
     def pick_r(self, problem: Problem, t: float, eps: float = 1e-3, margin: float | None = None, r_max: int = 4096):
@@ -281,10 +280,9 @@ def sweep(problem: Problem, t: float, eps: float = 1e-3, r_max: int = 4096, dtyp
 
 
 def bound_r(problem: Problem, t: float, eps: float = 1e-3) -> int:
-    """Step count from the analytic bound: eps = C delta^2 with delta = t / r
-    (the paper's error model), so r = ceil(t sqrt(C / eps))."""
-    C = problem.ham.trotter_bound()
-    return max(1, int(math.ceil(t * math.sqrt(C / eps))))
+    """Step count from the analytic bound (ps_ham_bound_steps): eps = C delta^2
+    with delta = t / r (the paper's error model), so r = ceil(t sqrt(C / eps))."""
+    return _lib.ps_ham_bound_steps(problem.ham.handle, t, eps)
 
 
 def run_error(problem: Problem, t: float, r: int, g_ref: complex, dtype=None) -> float:

@@ -368,3 +368,33 @@ def test_split_optimizer_matches_enumeration_with_the_oracle_bound():
     assert ps.ps_partial_optimize_split(H.handle, 1e-3, 1e-6, 1e6)[0] == len(h)
     assert lam > 0
 
+
+
+def test_learned_labels_margin_and_bound_steps_match_the_oracle():
+    """The arithmetic of the learned step choice sits behind the C ABI:
+    Richardson limit, error labels, pick margin and the bound's step count
+    against the oracle's versions."""
+    from oracle import learned as OL
+    rng = np.random.default_rng(90)
+    for _ in range(20):
+        g = rng.normal(size=3) + 1j * rng.normal(size=3)
+        assert abs(ps.ps_richardson3(*g) - OL.richardson3(*g)) < 1e-13 * (1 + np.max(np.abs(g)))
+    g = rng.normal(size=9) + 1j * rng.normal(size=9)
+    g[4] = 0.3 + 0.1j
+    eps, lg = _lib.ps_trotter_error_labels(g, 0.3 + 0.1j, 1e-12)
+    eps_o, lg_o = OL.error_labels(g, 0.3 + 0.1j, 1e-12)
+    assert np.allclose(eps, eps_o, rtol=1e-15, atol=0) and eps[4] == 0.0
+    assert lg.dtype == np.float32 and np.array_equal(lg, lg_o.astype(np.float32))
+    for n_rows, q in ((1, 0.8), (7, 0.8), (200, 0.8), (200, 0.5), (201, 0.05), (50, 1.0), (50, 0.0)):
+        y = rng.normal(size=n_rows).astype(np.float32)
+        pr = rng.normal(size=n_rows).astype(np.float32)
+        assert abs(_lib.ps_mlp_margin(y, pr, q) - OL.margin(y, pr, q)) < 1e-12
+    with pytest.raises(ps.PsError):
+        _lib.ps_mlp_margin(np.zeros(0, np.float32), np.zeros(0, np.float32), 0.8)
+    n = 9
+    x, z, h = inputs.jw_hamiltonian(n, 60, seed=91)
+    H = ps.Hamiltonian(n, x, z, h)
+    for t, e in ((0.1, 1e-3), (1.0, 1e-3), (2.5, 1e-2), (1e-6, 10.0)):
+        assert _lib.ps_ham_bound_steps(H.handle, t, e) == OL.bound_steps(n, x, z, h, t, e)
+    with pytest.raises(ps.PsError):
+        _lib.ps_ham_bound_steps(H.handle, 0.0, 1e-3)

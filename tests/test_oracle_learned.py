@@ -174,3 +174,38 @@ def test_adam_first_step_closed_form():
         step = q - q_new
         q = q_new
     assert np.allclose(step, lr * np.sign(g), rtol=1e-6)
+
+
+def test_richardson_limit_is_exact_for_the_first_order_error_form():
+    """g_r = g + a/r + b/r^2 exactly: the three-run limit is g (closed form),
+    for any R; an r^-3 term leaves an error that falls 8x per doubling of R."""
+    g, a, b = 0.3 - 0.2j, 1.7 + 0.4j, -2.5 + 1.1j
+    for R in (1.0, 8.0, 32.0):
+        gr = [g + a / r + b / r ** 2 for r in (R, 2 * R, 4 * R)]
+        assert abs(L.richardson3(*gr, R=R) - g) < 1e-13
+        assert abs(L.richardson3(*gr) - g) < 1e-12  # the limit does not depend on R
+    c = 3.0
+    err = []
+    for R in (8.0, 16.0, 32.0):
+        gr = [g + a / r + b / r ** 2 + c / r ** 3 for r in (R, 2 * R, 4 * R)]
+        err.append(abs(L.richardson3(*gr, R=R) - g))
+    assert 7.5 < err[0] / err[1] < 8.5 and 7.5 < err[1] / err[2] < 8.5
+
+
+def test_labels_margin_and_bound_steps_closed_forms():
+    # labels: g_r = g_lim + a/r gives log eps = log|a| - log r; the floor caps small errors
+    a = 0.02 - 0.01j
+    g = [0.5 + a / r for r in (1, 2, 4)] + [0.5 + 1e-20]
+    eps, lg = L.error_labels(g, 0.5, 1e-12)
+    assert np.allclose(eps[:3], abs(a) / np.array([1, 2, 4]), rtol=1e-14)
+    assert np.allclose(lg[:3], math.log(abs(a)) - np.log([1, 2, 4]), rtol=1e-14)
+    assert lg[3] == math.log(1e-12)
+    # margin: residuals 0..99, the 0.8 quantile at position 79.2; all-negative residuals give 0
+    y = np.arange(100, dtype=np.float64)
+    assert abs(L.margin(y, np.zeros(100), 0.8) - 79.2) < 1e-12
+    assert L.margin(-y - 1, np.zeros(100), 0.8) == 0.0
+    # bound steps: H = 0.5 X + 0.25 Z anticommute, C = 4 (0.5 * 0.25 + 0.25 * 0.5) = 1
+    assert L.trotter_bound(1, [1, 0], [0, 1], [0.5, 0.25]) == 1.0
+    assert L.bound_steps(1, [1, 0], [0, 1], [0.5, 0.25], 1.0, 1e-3) == 32   # ceil(sqrt(1000))
+    assert L.bound_steps(1, [1, 0], [0, 1], [0.5, 0.25], 2.0, 1e-3) == 64   # ceil(63.25)
+    assert L.bound_steps(1, [1, 0], [0, 1], [0.5, 0.25], 1e-3, 1.0) == 1
