@@ -402,8 +402,18 @@ def run_ours(args):
         diff = torch.linalg.vector_norm(psi.tensor.to(torch.complex128) * psi.scale() - p64.tensor * p64.scale()).item()
         ref = torch.linalg.vector_norm(p64.tensor * p64.scale()).item()
         tile64 = st64["kernel_ms"]["tile"] / max(st64["launches"]["tile"], 1)
-        fp64 = {"value": nrot / (ms64 / 1e3), "unit": UNIT, "dtype": "f64", "rotations": nrot,
-                "rot_per_pass": sum(pl.info["rotations"] for pl in plans64) / max(1, sum(pl.info["windows"] for pl in plans64)),
+        # ALU roofline of the complex128 pass: two FP64 FMAs (4 flops) per amplitude and
+        # rotation, plus the stored-scale FMA pair (4 flops) per amplitude and pass
+        rpp64 = sum(pl.info["rotations"] for pl in plans64) / max(1, sum(pl.info["windows"] for pl in plans64))
+        fma_peak = ps.ps_measure_fma_rate(ps.PS_C128)
+        flops_pass = (4.0 * rpp64 + 4.0) * (1 << N_QUBITS)
+        ach_tf = flops_pass / (tile64 / 1e3) / 1e12 if tile64 > 0 else None
+        fp64_roof = {"bound": "alu", "kernel": "k_tile<double,3,2>", "achieved": ach_tf, "peak": fma_peak,
+                     "unit": "TFLOP/s", "frac": ach_tf / fma_peak if ach_tf else None,
+                     "peak_source": "measured FP64 FMA throughput (ps_measure_fma_rate, this run)",
+                     "flops_per_launch": flops_pass}
+        fp64 = {"value": nrot / (ms64 / 1e3), "unit": UNIT, "dtype": "f64", "rotations": nrot, "roofline": fp64_roof,
+                "rot_per_pass": rpp64,
                 "tile_avg_launch_ms": tile64,
                 "tile_achieved_gbs": 2.0 * 16.0 * (1 << N_QUBITS) / (tile64 / 1e3) / 1e9 if tile64 > 0 else None,
                 "bound": "alu (FP64 pipe)",

@@ -81,10 +81,6 @@ typedef struct ps_tuning {
                           default is capped to it).  Fewer threads give each thread more
                           register batches per round, spreading its fixed per-round work over
                           more amplitudes. */
-    int test_extra_tx; /* test hook, 0 in normal use: bytes (0..4096) that a tile pass staged
-                          by bulk copies waits for beyond its tile.  They never arrive, so the
-                          pass's bounded wait runs out (about 1 s), the pass stores nothing and
-                          the next synchronising call returns PS_ERR_TIMEOUT. */
 } ps_tuning;
 
 /* Counters of a state handle since creation or the last ps_reset_stats. */
@@ -202,6 +198,15 @@ int ps_plan_export(int n, int dtype, const uint64_t *x, const uint64_t *z, const
  * to 1 and ps_copy_state copies it.  This removes the systematic norm drift
  * that per-rotation rounding of cos(phi) ~ 1 to FP32 would cause. */
 int ps_get_scale(const ps_state *st, double *out);
+
+/* Measurement helper (no counterpart in the paper): the current device's
+ * fused multiply-add throughput in TFLOP/s (2 flops per FMA) for the
+ * arithmetic of a dtype -- FP32 for PS_C64, FP64 for PS_C128 -- from
+ * independent FMA chains in every thread of a full grid, best of three
+ * launches timed with CUDA events (about 0.1 s each).  It is the peak of the
+ * ALU roofline of a tile pass whose arithmetic, not HBM, bounds it (the
+ * complex128 pass on GB300).  Synchronises the device's default stream. */
+int ps_measure_fma_rate(int dtype, double *tflops_out);
 
 /* ------------------------------------------------------------ reductions */
 
@@ -357,24 +362,48 @@ int ps_partial_optimize_split(const ps_ham *ham, double eps, double a, double b,
 
 /* ----------------------------------------------------- sharded schedule
  *
- * A state of n qubits spread over 2^m ranks by its upper m qubits (rank rho
- * holds amplitudes k with k >> (n - m) = rho), as the paper distributes it
- * over nodes (Results, Eq. 1).  ps_shard_plan splits a rotation sequence
- * into windows for rank `rank`: a window is a maximal run of rotations whose
- * X masks have one common nonzero part X above bit n - m (or none).  For a
- * window with X, the rank exchanges its slab with rank rho ^ X once (one
- * point-to-point send and receive of 2^(n-m) amplitudes) and applies the
- * window's rotations to the two slabs as one state of n - m + 1 qubits: its
- * own slab as the half with local top bit 0, the partner's as the half with
- * bit 1.  It keeps its own half; the partner does the same with the roles
- * swapped.  A window without X is applied to the slab alone (n - m qubits).
- * Outputs, for window w: partner[w] (-1: local), win_end[w] (one past its
- * last rotation); for every rotation: its local masks and angle (the upper
- * Z bits become a sign of the angle or the local top Z bit; see
- * csrc/ps_shard.cpp).  Arrays sized `count` (windows <= rotations). */
-int ps_shard_plan(int n, int m, int rank, const uint64_t *x, const uint64_t *z, const double *phi, size_t count,
-                  size_t *n_windows, int32_t *partner, uint64_t *win_end, uint64_t *x_out, uint64_t *z_out,
-                  double *phi_out);
+ * A state of n qubits spread over 2^m ranks, as the paper distributes it
+ * over nodes (Results, Eq. 1 and its proof in the Supplementary Methods):
+ * physical positions 0 .. s-1 (s = n - m) index amplitudes inside a rank's
+ * slab of 2^s, positions s .. n-1 are the bits of the rank.  layout[q] is the
+ * position of logical qubit q (the identity to start with).
+ *
+ * ps_shard_swap_plan splits a rotation sequence into steps for rank `rank`:
+ *   kind 0, window: rotations [arg_a, arg_b), to be applied to the slab with
+ *     the local masks x_out, z_out and the angles phi_out of those indices.
+ *     Every X mask of the window is local; Z bits at rank positions only flip
+ *     the angle's sign on ranks with odd popc(rank & z_rank) (the +-phi of
+ *     Eq. 1 with a diagonal Q).
+ *   kind 1, exchange before the next window: swap the rank positions of
+ *     mask arg_a with the slab positions of mask arg_b, paired in ascending
+ *     order (k = popc(arg_a) <= k_max pairs).  It is one all-to-all among the
+ *     2^k ranks that differ only in the swapped rank bits: ps_shard_pack
+ *     orders the slab into 2^k parts (part j goes to the rank whose swapped
+ *     bits spell j; the own part stays), and ps_shard_unpack places the part
+ *     received from the rank whose swapped bits spell j' -- so every rank
+ *     sends and receives (1 - 2^-k) of its slab.
+ * A window runs as long as its X masks touch at most k_max rank positions
+ * and enough slab qubits stay untouched to swap out; the slab qubits that
+ * leave are those whose next use by an X mask lies furthest ahead.  layout
+ * is updated to the final layout (pass it to the next call to continue).
+ * Arrays: kind, arg_a, arg_b hold up to 2 count entries; x_out, z_out,
+ * phi_out count.  Host only.  PS_ERR_ARG for m outside [1, min(n - 1, 20)],
+ * k_max outside [1, m], a rank outside [0, 2^m), masks with bits >= n, an X
+ * mask on more than n - m qubits (no slab can hold its pairs) or a layout
+ * that is not a permutation. */
+int ps_shard_swap_plan(int n, int m, int k_max, int rank, const uint64_t *x, const uint64_t *z, const double *phi,
+                       size_t count, int32_t *layout, size_t *n_steps, int32_t *kind, uint64_t *arg_a,
+                       uint64_t *arg_b, uint64_t *x_out, uint64_t *z_out, double *phi_out);
+
+/* The exchange's data movement on one rank's slab of 2^s amplitudes (dtype
+ * PS_C64 / PS_C128, device buffers, distinct, asynchronous on `stream`);
+ * lmask: the k slab positions being swapped (1 <= k <= min(20, s)).
+ *   pack:   out[j 2^(s-k) + c] = slab[the index with the bits of j at lmask and c in the other bits]
+ *   unpack: slab[that index] = in[j 2^(s-k) + c]
+ * The caller sends part j of `out` to the rank whose swapped bits spell j
+ * and gathers the received parts (and its own) into `in` by the same j. */
+int ps_shard_pack(int s, int dtype, uint64_t lmask, const void *slab_dev, void *out_dev, void *stream);
+int ps_shard_unpack(int s, int dtype, uint64_t lmask, const void *in_dev, void *slab_dev, void *stream);
 
 /* ------------------------------------------------------------ statistics */
 

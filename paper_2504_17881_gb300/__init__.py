@@ -13,7 +13,7 @@ from __future__ import annotations
 from . import _lib
 from ._lib import (PS_C64, PS_C128, PS_ERR_ARG, PS_ERR_TIMEOUT, PsError, ps_abi_version, ps_apply_rotations, ps_copy_state, ps_create,  # noqa: F401
                    ps_destroy, ps_device_count, ps_evolve_partial, ps_evolve_qdrift, ps_evolve_trotter,
-                   ps_get_scale, ps_get_state, ps_get_state_represented, ps_get_stats, ps_ham_create, ps_ham_destroy, ps_ham_lambda, ps_last_error, ps_norm,
+                   ps_get_scale, ps_get_state, ps_get_state_represented, ps_measure_fma_rate, ps_get_stats, ps_ham_create, ps_ham_destroy, ps_ham_lambda, ps_last_error, ps_norm,
                    ps_overlap, ps_overlap_noalloc, ps_partial_length, ps_partial_stream, ps_plan_apply, ps_plan_create, ps_plan_describe,
                    ps_plan_destroy, ps_plan_export, ps_plan_get_info, ps_qdrift_stream, ps_reset_stats,
                    ps_set_state, ps_set_tuning, ps_batch_create, ps_batch_launch, ps_batch_wait, ps_batch_run,
@@ -25,7 +25,8 @@ from ._lib import (PS_C64, PS_C128, PS_ERR_ARG, PS_ERR_TIMEOUT, PsError, ps_abi_
                    ps_mlp_adam_step, ps_mlp_train, ps_mlp_predict, ps_mlp_pick_r,
                    ps_mlp_pick_r_ensemble, ps_evolve_trotter2, ps_evolve_partial2, ps_trotter2_length,
                    ps_trotter2_stream, ps_partial2_length, ps_partial2_stream, ps_ham_sort_lexicographic,
-                   ps_rpe_signal, ps_rpe_estimate, ps_partial_optimize_split, ps_shard_plan, ps_richardson3,
+                   ps_rpe_signal, ps_rpe_estimate, ps_partial_optimize_split, ps_shard_swap_plan, ps_shard_pack,
+                   ps_shard_unpack, ps_richardson3,
                    ps_ham_bound_steps, ps_trotter_error_labels, ps_mlp_margin, ps_mlp_predict_ensemble)
 
 __all__ = [n for n in dir(_lib) if n.startswith("ps_")] + ["StateVector", "Hamiltonian", "Plan", "Batch",

@@ -30,7 +30,7 @@ class PsError(RuntimeError):
 class ps_tuning(ctypes.Structure):
     _fields_ = [("tile_bits", ctypes.c_int), ("group_bits", ctypes.c_int), ("max_window", ctypes.c_int),
                 ("pair_single", ctypes.c_int), ("kernel_timing", ctypes.c_int), ("reg_groups", ctypes.c_int),
-                ("seg_bits", ctypes.c_int), ("tile_threads", ctypes.c_int), ("test_extra_tx", ctypes.c_int)]
+                ("seg_bits", ctypes.c_int), ("tile_threads", ctypes.c_int)]
 
 
 class ps_stats(ctypes.Structure):
@@ -90,6 +90,7 @@ _SIGS = {
     "ps_set_state": (_i, [_vp, _vp]),
     "ps_get_state": (_i, [_vp, _vp]),
     "ps_get_state_represented": (_i, [_vp, _vp]),
+    "ps_measure_fma_rate": (_i, [_i, ctypes.POINTER(_d)]),
     "ps_copy_state": (_i, [_vp, _vp]),
     "ps_set_tuning": (_i, [_vp, ctypes.POINTER(ps_tuning)]),
     "ps_apply_rotations": (_i, [_vp, _vp, _vp, _vp, _sz]),
@@ -132,7 +133,10 @@ _SIGS = {
     "ps_ham_sort_lexicographic": (_i, [_vp]),
     "ps_rpe_signal": (_i, [_vp, _vp, _vp, _i, _sz, _d, _u32, _u64, _u64, _vp]),
     "ps_rpe_estimate": (_i, [_vp, _u32, _d, ctypes.POINTER(_d), _vp]),
-    "ps_shard_plan": (_i, [_i, _i, _i, _vp, _vp, _vp, _sz, ctypes.POINTER(_sz), _vp, _vp, _vp, _vp, _vp]),
+    "ps_shard_swap_plan": (_i, [_i, _i, _i, _i, _vp, _vp, _vp, _sz, _vp, ctypes.POINTER(_sz), _vp, _vp, _vp, _vp,
+                                _vp, _vp]),
+    "ps_shard_pack": (_i, [_i, _i, _u64, _vp, _vp, _vp]),
+    "ps_shard_unpack": (_i, [_i, _i, _u64, _vp, _vp, _vp]),
     "ps_partial_optimize_split": (_i, [_vp, _d, _d, _d, ctypes.POINTER(_sz), ctypes.POINTER(_d), ctypes.POINTER(_d)]),
     "ps_ham_trotter_bound": (_i, [_vp, _sz, ctypes.POINTER(_d)]),
     "ps_ham_bound_steps": (_i, [_vp, _d, _d, ctypes.POINTER(ctypes.c_uint32)]),
@@ -223,6 +227,13 @@ def ps_get_state(h: int, host_ptr: int):
 
 def ps_get_state_represented(h: int, host_ptr: int):
     _check(lib.ps_get_state_represented(ctypes.c_void_p(h), ctypes.c_void_p(host_ptr)))
+
+
+def ps_measure_fma_rate(dtype: int) -> float:
+    """FMA throughput of the current device in TFLOP/s (FP32 for PS_C64, FP64 for PS_C128)."""
+    out = _d()
+    _check(lib.ps_measure_fma_rate(dtype, ctypes.byref(out)))
+    return out.value
 
 
 def ps_copy_state(dst: int, src: int):
@@ -746,23 +757,38 @@ def ps_partial_optimize_split(ham: int, eps: float, a: float, b: float):
     return int(L_D.value), d.value, c.value
 
 
-def ps_shard_plan(n: int, m: int, rank: int, x, z, phi):
-    """Windows of a rotation sequence for one rank of 2^m: a list of
-    (partner or -1, local x, local z, local phi)."""
+def ps_shard_swap_plan(n: int, m: int, k_max: int, rank: int, x, z, phi, layout=None):
+    """Steps of the qubit-swap schedule for one rank of 2^m:
+    (steps, layout) with steps a list of ("exchange", rank-position mask, slab-position mask)
+    and ("window", local x, local z, local phi); layout the final one."""
     x, z, phi = _u64a(x), _u64a(z), _f64a(phi)
     cnt = len(phi)
-    nw = _sz()
-    partner = np.zeros(max(cnt, 1), dtype=np.int32)
-    end = np.zeros(max(cnt, 1), dtype=np.uint64)
+    lay = np.arange(n, dtype=np.int32) if layout is None else np.array(layout, dtype=np.int32, copy=True)
+    ns = _sz()
+    kind = np.zeros(max(2 * cnt, 1), dtype=np.int32)
+    a = np.zeros(max(2 * cnt, 1), dtype=np.uint64)
+    b = np.zeros(max(2 * cnt, 1), dtype=np.uint64)
     xo = np.zeros(max(cnt, 1), dtype=np.uint64)
     zo = np.zeros(max(cnt, 1), dtype=np.uint64)
     po = np.zeros(max(cnt, 1), dtype=np.float64)
-    _check(lib.ps_shard_plan(n, m, rank, _ptr(x), _ptr(z), _ptr(phi), cnt, ctypes.byref(nw), _ptr(partner), _ptr(end),
-                             _ptr(xo), _ptr(zo), _ptr(po)))
-    out, start = [], 0
-    for w in range(nw.value):
-        e = int(end[w])
-        out.append((int(partner[w]), xo[start:e].copy(), zo[start:e].copy(), po[start:e].copy()))
-        start = e
-    return out
+    _check(lib.ps_shard_swap_plan(n, m, k_max, rank, _ptr(x), _ptr(z), _ptr(phi), cnt, _ptr(lay), ctypes.byref(ns),
+                                  _ptr(kind), _ptr(a), _ptr(b), _ptr(xo), _ptr(zo), _ptr(po)))
+    steps = []
+    for t in range(ns.value):
+        if kind[t] == 1:
+            steps.append(("exchange", int(a[t]), int(b[t])))
+        else:
+            lo, hi = int(a[t]), int(b[t])
+            steps.append(("window", xo[lo:hi].copy(), zo[lo:hi].copy(), po[lo:hi].copy()))
+    return steps, lay
+
+
+def ps_shard_pack(s: int, dtype: int, lmask: int, slab_ptr: int, out_ptr: int, stream: int | None):
+    _check(lib.ps_shard_pack(s, dtype, lmask, ctypes.c_void_p(slab_ptr), ctypes.c_void_p(out_ptr),
+                             ctypes.c_void_p(stream or 0)))
+
+
+def ps_shard_unpack(s: int, dtype: int, lmask: int, in_ptr: int, slab_ptr: int, stream: int | None):
+    _check(lib.ps_shard_unpack(s, dtype, lmask, ctypes.c_void_p(in_ptr), ctypes.c_void_p(slab_ptr),
+                               ctypes.c_void_p(stream or 0)))
 

@@ -19,7 +19,7 @@ INCLUDE = os.path.join(ROOT, "include")
 OUT = os.path.join(PKG, "libps.so")
 BUILD_DIR = os.path.join(PKG, "_build")
 
-SOURCES = ["ps_tile.cu", "ps_stream.cu", "ps_batch.cu", "ps_noalloc.cu", "ps_mlp.cu", "ps_host.cpp",
+SOURCES = ["ps_tile.cu", "ps_stream.cu", "ps_batch.cu", "ps_noalloc.cu", "ps_mlp.cu", "ps_probe.cu", "ps_shardk.cu", "ps_host.cpp",
            "ps_batch_host.cpp", "ps_mlp_host.cpp", "ps_learn.cpp", "ps_shard.cpp", "ps_plan.cpp", "ps_sample.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

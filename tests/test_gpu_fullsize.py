@@ -219,3 +219,51 @@ def test_64bit_indices_sampled_amplitudes_vs_oracle(n, dtype):
     assert abs(st.norm2() - 1.0) < (1e-12 if dtype == ps.PS_C128 else 1e-5)
     del st
     torch.cuda.empty_cache()
+
+
+# ---------------- the n = 26 Trotter sweep's structure, against the oracle
+
+N_T = 24          # the largest n at which the oracle's 12,000 rotations take about a minute on 16 host cores
+T_TERMS = 2000    # the sweep's Hamiltonian: 2000 JW-like terms, seed 2, one-norm 3.5
+T_TIMES = (0.1, 0.1 * 2.0 ** 5)   # t_1 and t_16 of 0.1 * 2^(j/3)
+T_STEPS = (1, 2)
+
+
+@pytest.fixture(scope="module")
+def trotter_case():
+    x, z, h = inputs.jw_hamiltonian(N_T, T_TERMS, seed=2)
+    idx, amp = inputs.determinant_state(N_T, seed=21)
+    psi0 = np.zeros(1 << N_T, dtype=np.complex128)
+    psi0[idx.astype(np.int64)] = amp
+    ref = {}
+    oracle.set_threads(os.cpu_count() or 1)
+    try:
+        for t in T_TIMES:
+            for r in T_STEPS:
+                ref[(t, r)] = oracle.trotter(psi0, x, z, h, t, r)
+    finally:
+        oracle.set_threads(1)
+    return dict(x=x, z=z, h=h, idx=idx, amp=amp, psi0=psi0, ref=ref)
+
+
+@pytest.mark.parametrize("dtype", [ps.PS_C128, ps.PS_C64])
+def test_trotter_sweep_pairs_vs_oracle(trotter_case, dtype):
+    """(r in {1, 2}) x (t_1, t_16) of the first-order Trotter sweep, n = 24:
+    whole states and overlaps against the oracle's product formula (Eq. 3)."""
+    c = trotter_case
+    H = ps.Hamiltonian(N_T, c["x"], c["z"], c["h"])
+    st0 = sparse_state_on_gpu(N_T, dtype, c["idx"], c["amp"])
+    work = ps.StateVector(N_T, dtype=TDT[dtype])
+    for (t, r), ref in c["ref"].items():
+        work.copy_from(st0)
+        work.evolve_trotter(H, t, r)
+        g = work.overlap(st0)
+        got = work.to_numpy()
+        m = r * T_TERMS
+        tol = 1e-12 if dtype == ps.PS_C128 else math.sqrt(m) * 1e-7
+        assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < tol, (t, r)
+        g_ref = oracle.overlap(c["psi0"], ref)
+        assert abs(g - g_ref) / max(abs(g_ref), 1e-3) < tol, (t, r, g, g_ref)
+    del work, st0
+    H.close()
+    torch.cuda.empty_cache()

@@ -506,3 +506,4 @@ def test_rpe_signal_and_estimate_recover_the_trotter_eigenphase(dtype, tol):
     assert np.max(np.abs(Z - Z_ref)) < tol
     E, _ = ps.ps_rpe_estimate(Z, delta)
     assert abs(E * delta - theta0) <= np.arcsin(0.15 / 0.85) / 2.0 ** M + 1e-9
+
