@@ -51,6 +51,7 @@ REF_ROTATIONS_PER_STEP = 4
 FALLBACK_HBM_GBS = 6800.0
 BATCH_RUNS = 512
 BATCH_SEED = 5
+LEARNED_TIMES = (0.25, 0.5, 0.75, 1.0, 1.25, 1.5, 1.75, 2.0)  # the n = 32 step-choice queries
 
 
 def workload_name():
@@ -71,7 +72,7 @@ def parse():
     ap.add_argument("--fp64-rotations", type=int, default=SEG_LEN,
                     help="rotations of the stream run in complex128 and complex64 for the error report "
                          "(default one segment; 100000 for the whole run)")
-    ap.add_argument("--workload", choices=["qdrift30", "batched", "learned", "trotter26"], default="qdrift30",
+    ap.add_argument("--workload", choices=["qdrift30", "batched", "learned", "trotter26", "kernels"], default="qdrift30",
                     help="batched: 512 independent qDRIFT / partially randomised runs, n 14..22, in one "
                          "persistent launch (reported on its own JSON line)")
     ap.add_argument("--batch-runs", type=int, default=BATCH_RUNS)
@@ -708,7 +709,7 @@ def run_learned(args):
     x, z, h = inputs.jw_hamiltonian(n, 1000, seed=1500, lam=8.0)
     prob = learned.Problem(n, x, z, h, psi_seed=1500)
     queries = []
-    for t in (1.0, 2.0):
+    for t in LEARNED_TIMES:
         tq = time.perf_counter()
         r_ml, _ = m.pick_r(prob, t, eps)
         pick_s = time.perf_counter() - tq
@@ -753,6 +754,59 @@ def run_learned(args):
         "queries": queries, "rotations_sweep": tot_sw, "rotations_learned": tot_ml,
     }
     print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------- single-kernel timings
+
+def run_kernels(args):
+    """The pair-streaming kernel and the overlap reduction at n = 30 on their
+    own (CUDA events per launch, inputs far larger than L2): 64 single-rotation
+    windows with an X bit at the top qubit (so the tile kernel cannot take
+    them), then 8 overlaps, in complex64 and complex128.  Bytes: one read and
+    one write of every amplitude per pair launch, one read of both states per
+    overlap."""
+    import torch
+    import paper_2504_17881_gb300 as ps
+    from paper_2504_17881_gb300 import inputs
+    torch.cuda.set_device(0)
+    n = N_QUBITS
+    peak, peak_kind = hbm_peak()
+    rng = np.random.default_rng(77)
+    count = 64
+    x = (rng.integers(0, 1 << (n - 1), size=count, dtype=np.uint64) | np.uint64(1 << (n - 1))).astype(np.uint64)
+    z = rng.integers(0, 1 << n, size=count, dtype=np.uint64).astype(np.uint64)
+    phi = rng.uniform(-1e-3, 1e-3, size=count)
+    out = {}
+    for name, tdt, dt in (("c64", torch.complex64, ps.PS_C64), ("c128", torch.complex128, ps.PS_C128)):
+        S = 8 if name == "c64" else 16
+        a = ps.StateVector(n, dtype=tdt)
+        b = ps.StateVector(n, dtype=tdt)
+        a.tensor.fill_(1.0 / (1 << (n // 2)))
+        b.tensor.fill_(1.0 / (1 << (n // 2)))
+        a.set_tuning(kernel_timing=1, max_window=1)
+        plan = ps.Plan(n, dt, x, z, phi, tuning={"max_window": 1})
+        assert plan.info["pair_windows"] == count
+        a.apply_plan(plan)
+        a.overlap(b)
+        ps.ps_reset_stats(a.handle)
+        a.apply_plan(plan)
+        for _ in range(8):
+            a.overlap(b)
+        st = a.stats()
+        pair_ms = st["kernel_ms"]["pair"] / st["launches"]["pair"]
+        red_ms = st["kernel_ms"]["reduce"] / (st["launches"]["reduce"] / 2)
+        out[name] = {
+            "pair": {"launches": st["launches"]["pair"], "avg_launch_ms": pair_ms,
+                     "gbs": 2.0 * S * (1 << n) / (pair_ms / 1e3) / 1e9,
+                     "frac_of_copy": 2.0 * S * (1 << n) / (pair_ms / 1e3) / 1e9 / peak},
+            "overlap": {"calls": st["launches"]["reduce"] // 2, "avg_ms": red_ms,
+                        "gbs": 2.0 * S * (1 << n) / (red_ms / 1e3) / 1e9,
+                        "frac_of_copy": 2.0 * S * (1 << n) / (red_ms / 1e3) / 1e9 / peak}}
+        del a, b, plan
+        torch.cuda.empty_cache()
+    out["fma_tflops"] = {"fp32": ps.ps_measure_fma_rate(ps.PS_C64), "fp64": ps.ps_measure_fma_rate(ps.PS_C128)}
+    print(json.dumps({"metric": f"single kernels at n={n}: GB/s per launch", "peak_gbs": peak,
+                      "peak_source": peak_kind, "kernels": out}), flush=True)
 
 
 # ------------------------------------------------------------- Trotter n=26
@@ -910,6 +964,8 @@ def main():
         run_learned(args)
     elif args.workload == "trotter26":
         run_trotter26(args)
+    elif args.workload == "kernels":
+        run_kernels(args)
     else:
         run_ours(args)
 

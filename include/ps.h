@@ -131,7 +131,11 @@ void ps_destroy(ps_state *st);
 
 /* Copy 2^n amplitudes from / to host memory (pinned memory is fastest).
  * ps_set_state is asynchronous: host_src must stay valid until the stream
- * reaches the copy.  ps_get_state synchronises. */
+ * reaches the copy, and it resets the carried scale to 1.  ps_get_state
+ * synchronises and returns the STORED amplitudes: the represented state is
+ * ps_get_scale() times them (for PS_C64 the factor can differ from 1 by up
+ * to 2^-16, more than the complex64 tolerance), so compare with a reference
+ * through ps_get_state_represented. */
 int ps_set_state(ps_state *st, const void *host_src);
 int ps_get_state(ps_state *st, void *host_dst);
 

@@ -151,7 +151,32 @@ __device__ __forceinline__ void block_sum2(double &re, double &im, double *sh) {
     }
 }
 
-// what = 0: sum |a|^2 ; what = 1: sum conj(a) b.  FP64 products and sums.
+// Error-free transformations of FP32 values (Dekker's product, Knuth's sum):
+// a b = p + e exactly, and acc.hi + v = s + err exactly.  A float pair
+// (hi, lo) accumulates a few exact products with about 48 bits of precision;
+// it is folded into the FP64 sums every kFoldAmps amplitudes.
+struct FloatPair {
+    float hi, lo;
+};
+// The _rn intrinsics keep the compiler from fusing a product into a sum,
+// which would break the exactness of both transformations.
+__device__ __forceinline__ void pair_add_product(FloatPair &acc, float a, float b) {
+    const float p = __fmul_rn(a, b);
+    const float e = fmaf(a, b, -p);
+    const float s = __fadd_rn(acc.hi, p);
+    const float bb = __fsub_rn(s, acc.hi);
+    const float err = __fadd_rn(__fsub_rn(acc.hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+    acc.hi = s;
+    acc.lo = __fadd_rn(acc.lo, __fadd_rn(err, e));
+}
+constexpr int kFoldAmps = 16;
+
+// what = 0: sum |a|^2 ; what = 1: sum conj(a) b.
+// complex128: FP64 products and sums.  complex64: each product exact as a
+// float pair (its 48 significant bits fit FP64 as well), summed in a float
+// pair over kFoldAmps amplitudes, then added to the FP64 sums -- half an FP64
+// operation per amplitude instead of four conversions and four FP64 FMAs,
+// which left the reduction bound by GB300's FP64 pipe at about 1.1 TB/s.
 template <typename R, int WHAT>
 __global__ void __launch_bounds__(kReduceThreads) k_reduce1(const typename CT<R>::T *__restrict__ a,
                                                             const typename CT<R>::T *__restrict__ b, uint64_t N,
@@ -159,14 +184,51 @@ __global__ void __launch_bounds__(kReduceThreads) k_reduce1(const typename CT<R>
     __shared__ double sh[2 * kReduceThreads / 32];
     double re = 0.0, im = 0.0;
     const uint64_t stride = (uint64_t)gridDim.x * kReduceThreads;
-    for (uint64_t k = (uint64_t)blockIdx.x * kReduceThreads + threadIdx.x; k < N; k += stride) {
-        const double ar = (double)a[k].x, ai = (double)a[k].y;
-        if (WHAT == 0) {
-            re = fma(ar, ar, fma(ai, ai, re));
-        } else {
-            const double br = (double)b[k].x, bi = (double)b[k].y;
-            re = fma(ar, br, fma(ai, bi, re));
-            im = fma(ar, bi, fma(-ai, br, im));
+    if constexpr (sizeof(R) == 4) {
+        // two amplitudes per 16-byte load (N is even)
+        const float4 *a4 = reinterpret_cast<const float4 *>(a);
+        const float4 *b4 = reinterpret_cast<const float4 *>(b);
+        const uint64_t N2 = N >> 1;
+        FloatPair pr{0.f, 0.f}, pi{0.f, 0.f};
+        int folded = 0;
+        for (uint64_t k = (uint64_t)blockIdx.x * kReduceThreads + threadIdx.x; k < N2; k += stride) {
+            const float4 u = a4[k];
+            if (WHAT == 0) {
+                pair_add_product(pr, u.x, u.x);
+                pair_add_product(pr, u.y, u.y);
+                pair_add_product(pr, u.z, u.z);
+                pair_add_product(pr, u.w, u.w);
+            } else {
+                const float4 v = b4[k];
+                pair_add_product(pr, u.x, v.x);
+                pair_add_product(pr, u.y, v.y);
+                pair_add_product(pi, u.x, v.y);
+                pair_add_product(pi, -u.y, v.x);
+                pair_add_product(pr, u.z, v.z);
+                pair_add_product(pr, u.w, v.w);
+                pair_add_product(pi, u.z, v.w);
+                pair_add_product(pi, -u.w, v.z);
+            }
+            if (++folded == kFoldAmps / 2) {
+                re += (double)pr.hi + (double)pr.lo;
+                im += (double)pi.hi + (double)pi.lo;
+                pr = FloatPair{0.f, 0.f};
+                pi = FloatPair{0.f, 0.f};
+                folded = 0;
+            }
+        }
+        re += (double)pr.hi + (double)pr.lo;
+        im += (double)pi.hi + (double)pi.lo;
+    } else {
+        for (uint64_t k = (uint64_t)blockIdx.x * kReduceThreads + threadIdx.x; k < N; k += stride) {
+            const double ar = (double)a[k].x, ai = (double)a[k].y;
+            if (WHAT == 0) {
+                re = fma(ar, ar, fma(ai, ai, re));
+            } else {
+                const double br = (double)b[k].x, bi = (double)b[k].y;
+                re = fma(ar, br, fma(ai, bi, re));
+                im = fma(ar, bi, fma(-ai, br, im));
+            }
         }
     }
     block_sum2<kReduceThreads>(re, im, sh);
