@@ -544,7 +544,7 @@ def run_batched(args):
     cfg = None
     if not args.no_autotune:
         tune = autotune.tune_batch(runs, torch.complex64)
-        cfg = {"lane_size": tune["lane_size"], "tile_bits": tune["tile_bits"]}
+        cfg = {k: tune[k] for k in ("lane_size", "tile_bits", "single_bits") if k in tune}
     t_host = time.perf_counter()
     b = ps.Batch(runs, cfg=cfg)
     create_s = time.perf_counter() - t_host

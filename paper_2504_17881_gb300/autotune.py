@@ -1,12 +1,13 @@
-"""Autotuner of the batched launch: CTAs per lane and largest tile bits.
+"""Autotuner of the batched launch: CTAs per lane, largest tile bits, single-CTA size.
 
 The best lane size and tile size depend on the mix of run sizes: many small
 runs favour short lanes (more runs in flight, fewer idle members), a few
 large runs favour long lanes (each state's tiles spread over more SMs, fewer
 states competing for L2).  The tuner times whole batch launches on the device
-(CUDA events on the batch's stream, after one untimed launch) in two stages,
-lane size first and then tile bits at the best lane size, and caches the
-winner per device and batch signature in a JSON file.
+(CUDA events on the batch's stream, after one untimed launch) in three
+stages -- lane size, then tile bits at the best lane size, then the largest
+n run by one CTA alone (no lane barriers; longer single runs) -- and caches
+the winner per device and batch signature in a JSON file.
 
 Timing runs the real batch, so a tuning call costs a few launches of it per
 candidate plus the host schedule of each candidate (about a second for 512
@@ -22,6 +23,7 @@ from . import PS_C64, Batch
 
 LANE_SIZES = (8, 16, 32, 64)
 TILE_BITS = {PS_C64: (13, 12, 11, 10), 1: (12, 11, 10)}
+SINGLE_BITS = (None, 15, 16, 17)  # None: the library default (one above the resident size)
 
 
 def cache_file() -> str:
@@ -111,8 +113,16 @@ def tune_batch(runs, dtype=None, reps: int = 2, use_cache: bool = True, lane_siz
     best_lane = min(lane_sizes, key=lambda s: measure({"lane_size": s}))
     tbs = tile_bits or TILE_BITS[psd]
     best_tb = min(tbs, key=lambda t: measure({"lane_size": best_lane, "tile_bits": t}))
-    result = {"lane_size": best_lane, "tile_bits": best_tb, "ms": measure({"lane_size": best_lane, "tile_bits": best_tb}),
-              "timings_ms": timings, "signature": sig}
+
+    def with_single(sb):
+        cfg = {"lane_size": best_lane, "tile_bits": best_tb}
+        if sb is not None:
+            cfg["single_bits"] = sb
+        return cfg
+
+    best_sb = min(SINGLE_BITS, key=lambda sb: measure(with_single(sb)))
+    best = with_single(best_sb)
+    result = dict(best, ms=measure(best), timings_ms=timings, signature=sig)
     if use_cache:
         db = _load()
         db[sig] = result
