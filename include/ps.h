@@ -380,7 +380,8 @@ int ps_partial_optimize_split(const ps_ham *ham, double eps, double a, double b,
  *     Eq. 1 with a diagonal Q).
  *   kind 1, exchange before the next window: swap the rank positions of
  *     mask arg_a with the slab positions of mask arg_b, paired in ascending
- *     order (k = popc(arg_a) <= k_max pairs).  It is one all-to-all among the
+ *     order (k = popc(arg_a) pairs: at most k_max, more only when a single
+ *     rotation's X mask touches more rank positions).  It is one all-to-all among the
  *     2^k ranks that differ only in the swapped rank bits: ps_shard_pack
  *     orders the slab into 2^k parts (part j goes to the rank whose swapped
  *     bits spell j; the own part stays), and ps_shard_unpack places the part

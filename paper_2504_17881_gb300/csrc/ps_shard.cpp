@@ -11,6 +11,7 @@
 #include <algorithm>
 #include <cstring>
 #include <sstream>
+#include <vector>
 
 #include "ps_internal.h"
 
@@ -88,7 +89,15 @@ extern "C" int ps_shard_swap_plan(int n, int m, int k_max, int rank, const uint6
         return r;
     };
     const uint64_t local_mask = (1ull << s) - 1;
-    constexpr size_t kLookahead = 1 << 14;
+    // for every qubit, the rotations whose X mask uses it, in order (next-use queries)
+    std::vector<std::vector<uint32_t>> uses(n);
+    for (size_t r = 0; r < count; ++r)
+        for (uint64_t v = x[r]; v; v &= v - 1) uses[__builtin_ctzll(v)].push_back((uint32_t)r);
+    auto next_use_after = [&](int q, size_t e) -> size_t {
+        const auto &u = uses[q];
+        const auto it = std::lower_bound(u.begin(), u.end(), (uint32_t)e);
+        return it == u.end() ? (size_t)-1 : (size_t)*it;
+    };
     size_t ns = 0;
     size_t j = 0;
     while (j < count) {
@@ -117,10 +126,7 @@ extern "C" int ps_shard_swap_plan(int n, int m, int k_max, int rank, const uint6
             for (int p = s - 1; p >= 0; --p) {
                 const int q = inv[p];
                 if ((used >> q) & 1) continue;
-                size_t u = e;
-                const size_t stop = std::min(count, e + kLookahead);
-                while (u < stop && !((x[u] >> q) & 1)) ++u;
-                next_use[nc] = (u < stop) ? u : (size_t)-1;
+                next_use[nc] = next_use_after(q, e);
                 cand[nc++] = p;
             }
             // stable selection of the k furthest
