@@ -403,12 +403,19 @@ int ps_shard_swap_plan(int n, int m, int k_max, int rank, const uint64_t *x, con
 /* The exchange's data movement on one rank's slab of 2^s amplitudes (dtype
  * PS_C64 / PS_C128, device buffers, distinct, asynchronous on `stream`);
  * lmask: the k slab positions being swapped (1 <= k <= min(20, s)).
- *   pack:   out[j 2^(s-k) + c] = slab[the index with the bits of j at lmask and c in the other bits]
- *   unpack: slab[that index] = in[j 2^(s-k) + c]
- * The caller sends part j of `out` to the rank whose swapped bits spell j
- * and gathers the received parts (and its own) into `in` by the same j. */
-int ps_shard_pack(int s, int dtype, uint64_t lmask, const void *slab_dev, void *out_dev, void *stream);
-int ps_shard_unpack(int s, int dtype, uint64_t lmask, const void *in_dev, void *slab_dev, void *stream);
+ * Packed index i = j 2^(s-k) + c names amplitude c (in the order of the
+ * other bits) of part j (the amplitudes whose bits at lmask spell j); the
+ * calls move the packed range [first, first + count):
+ *   pack:   out[i - first] = slab[the index with the bits of j at lmask and c in the other bits]
+ *   unpack: slab[that index] = in[i - first]
+ * A whole exchange packs part j for the rank whose swapped bits spell j and
+ * unpacks, at part j', what the rank whose swapped bits spell j' sent; done
+ * part by part (the own part stays), or in chunks of a part, a rank needs two
+ * chunk buffers beside its slab.  PS_ERR_ARG for a range outside 2^s. */
+int ps_shard_pack(int s, int dtype, uint64_t lmask, uint64_t first, uint64_t count, const void *slab_dev,
+                  void *out_dev, void *stream);
+int ps_shard_unpack(int s, int dtype, uint64_t lmask, uint64_t first, uint64_t count, const void *in_dev,
+                    void *slab_dev, void *stream);
 
 /* ------------------------------------------------------------ statistics */
 

@@ -135,8 +135,8 @@ _SIGS = {
     "ps_rpe_estimate": (_i, [_vp, _u32, _d, ctypes.POINTER(_d), _vp]),
     "ps_shard_swap_plan": (_i, [_i, _i, _i, _i, _vp, _vp, _vp, _sz, _vp, ctypes.POINTER(_sz), _vp, _vp, _vp, _vp,
                                 _vp, _vp]),
-    "ps_shard_pack": (_i, [_i, _i, _u64, _vp, _vp, _vp]),
-    "ps_shard_unpack": (_i, [_i, _i, _u64, _vp, _vp, _vp]),
+    "ps_shard_pack": (_i, [_i, _i, _u64, _u64, _u64, _vp, _vp, _vp]),
+    "ps_shard_unpack": (_i, [_i, _i, _u64, _u64, _u64, _vp, _vp, _vp]),
     "ps_partial_optimize_split": (_i, [_vp, _d, _d, _d, ctypes.POINTER(_sz), ctypes.POINTER(_d), ctypes.POINTER(_d)]),
     "ps_ham_trotter_bound": (_i, [_vp, _sz, ctypes.POINTER(_d)]),
     "ps_ham_bound_steps": (_i, [_vp, _d, _d, ctypes.POINTER(ctypes.c_uint32)]),
@@ -783,12 +783,14 @@ def ps_shard_swap_plan(n: int, m: int, k_max: int, rank: int, x, z, phi, layout=
     return steps, lay
 
 
-def ps_shard_pack(s: int, dtype: int, lmask: int, slab_ptr: int, out_ptr: int, stream: int | None):
-    _check(lib.ps_shard_pack(s, dtype, lmask, ctypes.c_void_p(slab_ptr), ctypes.c_void_p(out_ptr),
+def ps_shard_pack(s: int, dtype: int, lmask: int, first: int, count: int, slab_ptr: int, out_ptr: int,
+                  stream: int | None):
+    _check(lib.ps_shard_pack(s, dtype, lmask, first, count, ctypes.c_void_p(slab_ptr), ctypes.c_void_p(out_ptr),
                              ctypes.c_void_p(stream or 0)))
 
 
-def ps_shard_unpack(s: int, dtype: int, lmask: int, in_ptr: int, slab_ptr: int, stream: int | None):
-    _check(lib.ps_shard_unpack(s, dtype, lmask, ctypes.c_void_p(in_ptr), ctypes.c_void_p(slab_ptr),
+def ps_shard_unpack(s: int, dtype: int, lmask: int, first: int, count: int, in_ptr: int, slab_ptr: int,
+                    stream: int | None):
+    _check(lib.ps_shard_unpack(s, dtype, lmask, first, count, ctypes.c_void_p(in_ptr), ctypes.c_void_p(slab_ptr),
                                ctypes.c_void_p(stream or 0)))
 

@@ -2,18 +2,21 @@
 
 Each rank holds one slab of 2^(n-m) amplitudes.  The plan alternates
 windows, which every rank applies to its own slab with the single-GPU
-kernels, and exchanges, which swap rank bits with slab bits: the slab is
-packed into 2^k parts (ps_shard_pack), part j goes to the rank whose
-swapped bits spell j, and the parts received are placed back
-(ps_shard_unpack).  The arithmetic and the data movement run in libps; this
-module arranges the calls and hands the parts to a communication callback:
+kernels, and exchanges, which swap k rank bits with k slab bits.  An
+exchange runs as 2^k - 1 pairwise rounds: in round t the rank whose swapped
+bits spell j trades part j ^ t of its slab (the amplitudes whose swapped
+slab bits spell j ^ t) with the rank whose swapped bits spell j ^ t, which
+sends its part j back; the received part lands where the sent one was.
+Every part moves in chunks through two chunk buffers, so a rank needs its
+slab plus two chunks, and the arithmetic and the data movement run in libps
+(ps_shard_pack / ps_shard_unpack); this module arranges the calls and hands
+each chunk to a communication callback:
 
-  exchange(parts, partners) -> received parts, parts[j] sent to partners[j]
-      and received[j] from partners[j] (partners[j] == rank: the own part)
+  exchange(send, partner) -> the partner's chunk (the partner sends ours)
 
 `torch_exchange` does it with torch.distributed point-to-point messages
 (NCCL between GPUs, gloo between CPU processes); `libps_moves` gives the
-pack / unpack / apply callbacks on a CUDA slab.
+pack / unpack callbacks on a CUDA slab.
 """
 from __future__ import annotations
 
@@ -29,55 +32,62 @@ def set_bits(mask: int) -> list[int]:
     return out
 
 
-def exchange_partners(rank: int, s: int, rank_mask: int) -> list[int]:
-    """Rank receiving part j of an exchange over the rank positions of rank_mask
-    (ascending): `rank` with bit t of j at the t-th swapped rank bit."""
-    gbits = [p - s for p in set_bits(rank_mask)]
-    out = []
-    for j in range(1 << len(gbits)):
-        r = rank
-        for t, b in enumerate(gbits):
-            r = (r & ~(1 << b)) | (((j >> t) & 1) << b)
-        out.append(r)
-    return out
+def swapped_bits(rank: int, s: int, rank_mask: int) -> int:
+    """The value j that the swapped rank bits of `rank` spell (t-th lowest bit <-> t-th swapped position)."""
+    j = 0
+    for t, p in enumerate(set_bits(rank_mask)):
+        j |= ((rank >> (p - s)) & 1) << t
+    return j
+
+
+def rank_with_bits(rank: int, s: int, rank_mask: int, j: int) -> int:
+    """`rank` with its swapped bits replaced by the bits of j."""
+    for t, p in enumerate(set_bits(rank_mask)):
+        b = p - s
+        rank = (rank & ~(1 << b)) | (((j >> t) & 1) << b)
+    return rank
+
+
+def exchange_rounds(rank: int, s: int, rank_mask: int):
+    """(partner, part index) of rounds t = 1 .. 2^k - 1 of one exchange."""
+    k = bin(rank_mask).count("1")
+    own = swapped_bits(rank, s, rank_mask)
+    return [(rank_with_bits(rank, s, rank_mask, own ^ t), own ^ t) for t in range(1, 1 << k)]
 
 
 def run_sharded(n: int, m: int, rank: int, slab, x, z, phi, exchange, apply, pack, unpack, k_max: int | None = None,
-                layout=None):
+                layout=None, chunk_bits: int | None = None):
     """Evolve this rank's slab through the sequence; returns (slab, layout).
-    apply(slab, x, z, phi) -> slab;  pack(slab, slab_mask) -> parts (a sequence of 2^k);
-    unpack(parts, slab_mask, slab) -> slab."""
+    apply(slab, x, z, phi) -> slab;  pack(slab, slab_mask, first, count) -> chunk;
+    unpack(chunk, slab_mask, first, slab) -> slab (packed ranges, see ps_shard_pack).
+    chunk_bits: log2 of the amplitudes per message (default: a whole part)."""
     s = n - m
     steps, layout = ps_shard_swap_plan(n, m, m if k_max is None else k_max, rank, x, z, phi, layout)
     for st in steps:
         if st[0] == "window":
             if len(st[3]):
                 slab = apply(slab, st[1], st[2], st[3])
-        else:
-            _, rank_mask, slab_mask = st
-            parts = pack(slab, slab_mask)
-            received = exchange(parts, exchange_partners(rank, s, rank_mask))
-            slab = unpack(received, slab_mask, slab)
+            continue
+        _, rank_mask, slab_mask = st
+        k = bin(rank_mask).count("1")
+        part = 1 << (s - k)
+        chunk = part if chunk_bits is None else min(part, 1 << chunk_bits)
+        for partner, j in exchange_rounds(rank, s, rank_mask):
+            for c0 in range(0, part, chunk):
+                first = j * part + c0
+                got = exchange(pack(slab, slab_mask, first, chunk), partner)
+                slab = unpack(got, slab_mask, first, slab)
     return slab, layout
 
 
 def torch_exchange(dist):
-    """All parts of one exchange as batched point-to-point messages."""
-    def exchange(parts, partners):
+    """One chunk each way with the partner as a batched isend / irecv pair."""
+    def exchange(send, partner):
         import torch
-        me = dist.get_rank()
-        out = [None] * len(parts)
-        ops = []
-        for j, p in enumerate(partners):
-            if p == me:
-                out[j] = parts[j]
-            else:
-                out[j] = torch.empty_like(parts[j])
-                ops.append(dist.P2POp(dist.isend, parts[j].contiguous(), p))
-                ops.append(dist.P2POp(dist.irecv, out[j], p))
-        if ops:
-            for req in dist.batch_isend_irecv(ops):
-                req.wait()
+        out = torch.empty_like(send)
+        ops = [dist.P2POp(dist.isend, send.contiguous(), partner), dist.P2POp(dist.irecv, out, partner)]
+        for req in dist.batch_isend_irecv(ops):
+            req.wait()
         return out
     return exchange
 
@@ -89,15 +99,13 @@ def libps_moves(s: int, dtype: int, stream=None):
     def _stream():
         return (stream if stream is not None else torch.cuda.current_stream()).cuda_stream
 
-    def pack(slab, slab_mask):
-        k = bin(slab_mask).count("1")
-        out = torch.empty_like(slab)
-        ps_shard_pack(s, dtype, slab_mask, slab.data_ptr(), out.data_ptr(), _stream())
-        return list(out.view(1 << k, 1 << (s - k)).unbind(0))
+    def pack(slab, slab_mask, first, count):
+        out = torch.empty(count, dtype=slab.dtype, device=slab.device)
+        ps_shard_pack(s, dtype, slab_mask, first, count, slab.data_ptr(), out.data_ptr(), _stream())
+        return out
 
-    def unpack(parts, slab_mask, slab):
-        buf = torch.cat([p.reshape(-1) for p in parts])
-        ps_shard_unpack(s, dtype, slab_mask, buf.data_ptr(), slab.data_ptr(), _stream())
+    def unpack(chunk, slab_mask, first, slab):
+        ps_shard_unpack(s, dtype, slab_mask, first, chunk.numel(), chunk.data_ptr(), slab.data_ptr(), _stream())
         return slab
 
     return pack, unpack

@@ -45,21 +45,21 @@ def _insert(c, j, pos):
     return c
 
 
-def np_pack(slab, slab_mask):
+def _packed_at(slab, slab_mask, first, count):
+    """Slab indices of packed indices first .. first + count - 1 (part j, amplitude c: bits of j at slab_mask)."""
     pos = shard.set_bits(slab_mask)
     k, s = len(pos), slab.size.bit_length() - 1
-    idx = np.arange(1 << s, dtype=np.int64)
-    at = _insert(idx & ((1 << (s - k)) - 1), idx >> (s - k), pos)
-    return list(slab[at].reshape(1 << k, -1))
+    idx = np.arange(first, first + count, dtype=np.int64)
+    return _insert(idx & ((1 << (s - k)) - 1), idx >> (s - k), pos)
 
 
-def np_unpack(parts, slab_mask, slab):
-    pos = shard.set_bits(slab_mask)
-    k, s = len(pos), slab.size.bit_length() - 1
-    idx = np.arange(1 << s, dtype=np.int64)
-    at = _insert(idx & ((1 << (s - k)) - 1), idx >> (s - k), pos)
-    out = np.empty_like(slab)
-    out[at] = np.concatenate(parts)
+def np_pack(slab, slab_mask, first, count):
+    return slab[_packed_at(slab, slab_mask, first, count)].copy()
+
+
+def np_unpack(chunk, slab_mask, first, slab):
+    out = slab.copy()
+    out[_packed_at(slab, slab_mask, first, len(chunk))] = chunk
     return out
 
 
@@ -75,29 +75,34 @@ def to_logical(phys, layout):
     return out
 
 
-def emulate(n, m, psi, x, z, phi, apply, pack, unpack, k_max, layout=None):
-    """All 2^m ranks in lockstep: windows on every slab, exchanges between them.
-    psi is in the physical order of `layout` (identity when None)."""
+def emulate(n, m, psi, x, z, phi, apply, pack, unpack, k_max, layout=None, chunk_bits=None):
+    """All 2^m ranks in lockstep: windows on every slab; exchanges as the
+    pairwise rounds of shard.exchange_rounds, chunk by chunk, every pair
+    trading the chunks it packed.  psi is in the physical order of `layout`
+    (identity when None)."""
     s, R = n - m, 1 << m
     slabs = [psi[r << s:(r + 1) << s].copy() for r in range(R)]
     plans = [ps.ps_shard_swap_plan(n, m, k_max, r, x, z, phi, layout) for r in range(R)]
     layout = plans[0][1]
     assert all(np.array_equal(p[1], layout) for p in plans)
-    nsteps = len(plans[0][0])
-    for t in range(nsteps):
+    for t in range(len(plans[0][0])):
         st = plans[0][0][t]
         if st[0] == "window":
             slabs = [apply(slabs[r], *plans[r][0][t][1:]) if len(plans[r][0][t][3]) else slabs[r] for r in range(R)]
-        else:
-            _, rank_mask, slab_mask = st
-            parts = [pack(slabs[r], slab_mask) for r in range(R)]
-            new = []
+            continue
+        _, rank_mask, slab_mask = st
+        k = bin(rank_mask).count("1")
+        part = 1 << (s - k)
+        chunk = part if chunk_bits is None else min(part, 1 << chunk_bits)
+        rounds = [shard.exchange_rounds(r, s, rank_mask) for r in range(R)]
+        for q in range(len(rounds[0])):
             for r in range(R):
-                partners = shard.exchange_partners(r, s, rank_mask)
-                # received[j] = part sent by partners[j] to r: that rank's part with index "r's swapped bits"
-                mine = partners.index(r)
-                new.append(unpack([parts[p][mine] for p in partners], slab_mask, slabs[r]))
-            slabs = new
+                partner, j = rounds[r][q]
+                assert rounds[partner][q][0] == r  # the partner trades with r in the same round
+            for c0 in range(0, part, chunk):
+                sent = [pack(slabs[r], slab_mask, rounds[r][q][1] * part + c0, chunk) for r in range(R)]
+                slabs = [unpack(sent[rounds[r][q][0]], slab_mask, rounds[r][q][1] * part + c0, slabs[r])
+                         for r in range(R)]
     return np.concatenate(slabs), layout
 
 
@@ -106,12 +111,13 @@ def _emulate_from(n, m, phys, x, z, phi, layout):
                    layout)
 
 
-@pytest.mark.parametrize("n,m,k_max", [(6, 1, 1), (7, 2, 1), (7, 2, 2), (8, 3, 1), (8, 3, 3)])
-def test_swap_plan_reproduces_single_state_evolution(n, m, k_max):
+@pytest.mark.parametrize("n,m,k_max,chunk_bits", [(6, 1, 1, None), (7, 2, 1, None), (7, 2, 2, 2), (8, 3, 1, None),
+                                                  (8, 3, 3, 1)])
+def test_swap_plan_reproduces_single_state_evolution(n, m, k_max, chunk_bits):
     x, z, phi = sequence(n, 3 * n + m)
     psi = inputs.gaussian_state(n, 7)
     got, layout = emulate(n, m, psi, x, z, phi, lambda st, a, b, c: oracle.apply(st, a, b, c), np_pack, np_unpack,
-                          k_max)
+                          k_max, chunk_bits=chunk_bits)
     ref = oracle.apply(psi, x, z, phi)
     assert np.max(np.abs(to_logical(got, layout) - ref)) < 1e-13
 
@@ -198,13 +204,14 @@ def _gloo_rank(rank, world, port, n, out):
         def apply(st, a, b, c):
             return torch.as_tensor(oracle.apply(st.numpy(), a, b, c))
 
-        def pack(st, mask):
-            return [torch.as_tensor(p.copy()) for p in np_pack(st.numpy(), mask)]
+        def pack(st, mask, first, count):
+            return torch.as_tensor(np_pack(st.numpy(), mask, first, count))
 
-        def unpack(parts, mask, st):
-            return torch.as_tensor(np_unpack([p.numpy() for p in parts], mask, st.numpy()))
+        def unpack(chunk, mask, first, st):
+            return torch.as_tensor(np_unpack(chunk.numpy(), mask, first, st.numpy()))
 
-        res, layout = shard.run_sharded(n, m, rank, slab, x, z, phi, shard.torch_exchange(dist), apply, pack, unpack)
+        res, layout = shard.run_sharded(n, m, rank, slab, x, z, phi, shard.torch_exchange(dist), apply, pack, unpack,
+                                        chunk_bits=2)
         out[rank] = (res.numpy(), layout.tolist())
     finally:
         dist.destroy_process_group()
@@ -230,8 +237,10 @@ def test_gloo_ranks_exchange_parts(world):
 @pytest.mark.gpu
 @pytest.mark.parametrize("dtype,tol", [(torch.complex128, 1e-12), (torch.complex64, 1e-5)])
 def test_ranks_emulated_on_one_gpu_with_libps(dtype, tol):
-    """Every window through libps's tile and pair kernels on the rank's slab,
-    every exchange through the pack / unpack kernels."""
+    """Eight ranks on one GPU: every window through libps's tile and pair
+    kernels on the rank's slab (one StateVector per slab, so the carried scale
+    is the same on every rank), every exchange through the pack / unpack
+    kernels in chunks, the chunks routed between the ranks' device buffers."""
     n, m = 16, 3
     s = n - m
     x, z, h = inputs.jw_hamiltonian(n, 200, seed=51)
@@ -239,42 +248,28 @@ def test_ranks_emulated_on_one_gpu_with_libps(dtype, tol):
     psi = inputs.gaussian_state(n, 52)
     pdt = ps.PS_C64 if dtype == torch.complex64 else ps.PS_C128
     pack, unpack = shard.libps_moves(s, pdt)
-    states = {}
-
-    def apply(st, a, b, c):
-        sv = states.setdefault(st.data_ptr(), ps.StateVector(s, tensor=st))
-        sv.apply_rotations(a, b, c)
-        return st
-
-    def gpu_pack(st, mask):
-        # a windowed slab carries its own stored scale: fold it in before the amplitudes move
-        sv = states.pop(st.data_ptr(), None)
-        if sv is not None:
-            st = torch.as_tensor(sv.to_numpy()).to(dtype).cuda()
-        return pack(st, mask)
-
     R = 1 << m
-    slabs = [torch.as_tensor(psi[r << s:(r + 1) << s]).to(dtype).cuda() for r in range(R)]
+    svs = [ps.StateVector(s, tensor=torch.as_tensor(psi[r << s:(r + 1) << s]).to(dtype).cuda()) for r in range(R)]
     plans = [ps.ps_shard_swap_plan(n, m, m, r, xs, zs, ph) for r in range(R)]
     layout = plans[0][1]
+    chunk = 1 << 9
     for t in range(len(plans[0][0])):
         st = plans[0][0][t]
         if st[0] == "window":
             for r in range(R):
                 if len(plans[r][0][t][3]):
-                    slabs[r] = apply(slabs[r], *plans[r][0][t][1:])
-        else:
-            _, rank_mask, slab_mask = st
-            parts = [gpu_pack(slabs[r], slab_mask) for r in range(R)]
-            for r in range(R):
-                partners = shard.exchange_partners(r, s, rank_mask)
-                mine = partners.index(r)
-                slabs[r] = unpack([parts[p][mine] for p in partners], slab_mask,
-                                  torch.empty_like(parts[r][0]).repeat(len(partners)))
-    out = []
-    for r in range(R):
-        sv = states.get(slabs[r].data_ptr())
-        out.append(sv.to_numpy() if sv is not None else slabs[r].cpu().numpy().astype(np.complex128))
-    got = to_logical(np.concatenate(out), layout)
+                    svs[r].apply_rotations(*plans[r][0][t][1:])
+            continue
+        _, rank_mask, slab_mask = st
+        part = 1 << (s - bin(rank_mask).count("1"))
+        rounds = [shard.exchange_rounds(r, s, rank_mask) for r in range(R)]
+        for q in range(len(rounds[0])):
+            for c0 in range(0, part, min(chunk, part)):
+                cnt = min(chunk, part)
+                sent = [pack(svs[r].tensor, slab_mask, rounds[r][q][1] * part + c0, cnt) for r in range(R)]
+                for r in range(R):
+                    unpack(sent[rounds[r][q][0]], slab_mask, rounds[r][q][1] * part + c0, svs[r].tensor)
+    assert len({sv.scale() for sv in svs}) == 1
+    got = to_logical(np.concatenate([sv.to_numpy() for sv in svs]), layout)
     ref = oracle.apply(psi, xs, zs, ph)
     assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < tol
