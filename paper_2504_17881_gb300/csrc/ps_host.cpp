@@ -282,7 +282,7 @@ extern "C" {
 
 const char *ps_last_error(void) { return g_err.c_str(); }
 
-int ps_abi_version(void) { return 2; }
+int ps_abi_version(void) { return 3; }
 
 int ps_device_count(void) {
     int n = 0;

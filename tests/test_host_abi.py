@@ -41,7 +41,7 @@ def test_every_declared_symbol_is_exported():
 
 
 def test_abi_version_and_empty_error():
-    assert ps.ps_abi_version() == 2
+    assert ps.ps_abi_version() == 3
     assert isinstance(ps.ps_last_error(), str)
 
 
