@@ -398,3 +398,26 @@ def test_learned_labels_margin_and_bound_steps_match_the_oracle():
         assert _lib.ps_ham_bound_steps(H.handle, t, e) == OL.bound_steps(n, x, z, h, t, e)
     with pytest.raises(ps.PsError):
         _lib.ps_ham_bound_steps(H.handle, 0.0, 1e-3)
+
+
+def test_shard_moves_reject_bad_arguments_before_any_device_work():
+    """ps_shard_pack / ps_shard_unpack validate dtype, slab size, the swapped
+    positions and the packed range on the host; none of these calls touches
+    the (fake, never dereferenced) pointers."""
+    fake_a, fake_b = 1 << 20, 2 << 20
+    bad = [
+        (10, 7, 0b11, 0, 16),            # dtype
+        (0, ps.PS_C64, 0b1, 0, 1),        # s
+        (10, ps.PS_C64, 0, 0, 16),        # no swapped position
+        (10, ps.PS_C64, 1 << 10, 0, 16),  # a position at or above s
+        (10, ps.PS_C64, 0b11, 1000, 100), # range past 2^s
+    ]
+    for s, dt, lmask, first, count in bad:
+        with pytest.raises(ps.PsError):
+            _lib.ps_shard_pack(s, dt, lmask, first, count, fake_a, fake_b, None)
+        with pytest.raises(ps.PsError):
+            _lib.ps_shard_unpack(s, dt, lmask, first, count, fake_a, fake_b, None)
+    with pytest.raises(ps.PsError):  # source and destination must differ
+        _lib.ps_shard_pack(10, ps.PS_C64, 0b11, 0, 16, fake_a, fake_a, None)
+    with pytest.raises(ps.PsError):
+        _lib.ps_measure_fma_rate(5)
