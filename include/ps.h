@@ -196,9 +196,9 @@ int ps_plan_export(int n, int dtype, const uint64_t *x, const uint64_t *z, const
 /* Stored scale.  A pass applies the cos(phi) factors of its small-angle
  * rotations only to the precision the storage type represents; the residual
  * factor f is tracked in FP64 by the handle, so that the represented state is
- * f * (stored amplitudes).  f = 1 up to FP64 rounding for PS_C128; for
- * PS_C64, |f - 1| <= 2^-16 (the factor is applied once it exceeds that, as
- * a <- a + (f - 1) a, so that its rounding is unbiased).  ps_norm and ps_overlap include f; ps_set_state resets it
+ * f * (stored amplitudes).  |f - 1| <= 2^-20 for PS_C128 and 2^-16 for
+ * PS_C64 (the factor is applied once it exceeds that, as a <- a + (f - 1) a,
+ * so that its rounding is unbiased).  ps_norm and ps_overlap include f; ps_set_state resets it
  * to 1 and ps_copy_state copies it.  This removes the systematic norm drift
  * that per-rotation rounding of cos(phi) ~ 1 to FP32 would cause. */
 int ps_get_scale(const ps_state *st, double *out);

@@ -192,14 +192,17 @@ int launch_plan(ps_state *st, const Plan &p) {
             PS_CUDA(cudaEventRecord(ea, st->stream), "cudaEventRecord");
         }
         // Carry the window's cos(phi) product; apply it as a <- a + kdelta a
-        // (one rounding, unbiased) once it is far enough from 1 for the
-        // storage type -- always for complex128, beyond 2^-16 for complex64,
-        // where a factor within an ulp of 1 would round away systematically.
+        // (one rounding, unbiased) once it is far enough from 1: beyond 2^-16
+        // for complex64, where a factor within an ulp of 1 would round away
+        // systematically, and beyond 2^-20 for complex128, whose FP64 pass is
+        // bound by its FP64 arithmetic (applying the factor every pass would
+        // add two FMAs per amplitude to about eighteen).  Until then the
+        // stored amplitudes are the state divided by the carried factor.
         st->pending *= w.kprod;
         double kdelta = 0.0;
         const double dev = st->pending - 1.0;
         if (st->dtype == PS_C128) {
-            kdelta = dev;
+            if (std::fabs(dev) > 0x1.0p-20) kdelta = dev;
         } else if (std::fabs(dev) > 0x1.0p-16) {
             kdelta = (double)(float)dev;
         }
