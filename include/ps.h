@@ -632,6 +632,7 @@ size_t ps_mlp_num_params(const ps_mlp *m);
 int ps_mlp_get_params(ps_mlp *m, float *host);        /* synchronous */
 int ps_mlp_set_params(ps_mlp *m, const float *host);  /* synchronous */
 int ps_mlp_get_grads(ps_mlp *m, float *host);         /* gradient of the last ps_mlp_loss_grad */
+int ps_mlp_set_grads(ps_mlp *m, const float *host);   /* replace it (an externally accumulated gradient for ps_mlp_adam_step) */
 int ps_mlp_set_normalization(ps_mlp *m, const float *mu, const float *sigma, float y_mu, float y_sigma);
 int ps_mlp_get_normalization(const ps_mlp *m, float *mu, float *sigma, float *y_mu, float *y_sigma);
 /* mu and sigma (population standard deviation; 1 for a constant column) of

@@ -237,3 +237,49 @@ def amplitudes_sparse(n: int, idx0, amp0, x, z, phi, ks) -> np.ndarray:
     _check(_load().or_amplitudes_sparse(n, idx0.size, _p(idx0), _p(amp0), _p(x), _p(z), _p(phi),
                                         x.size, ks.size, _p(ks), _p(out)), "amplitudes_sparse")
     return out.view(np.complex128)
+
+
+def _one_norm(h) -> float:
+    """Sum of |h| in term order, one FP64 addition at a time (as the C sampler's cdf)."""
+    lam = 0.0
+    for v in h:
+        lam += abs(float(v))
+    return lam
+
+
+def qdrift_stream(x, z, h, t: float, N: int, seed: int, first: int = 0, count: int | None = None):
+    """Rotations first .. first + count - 1 of the qDRIFT run or_qdrift applies:
+    draw j picks term l with probability |h_l| / lambda (the oracle's own
+    sampler) and rotates by sgn(h_l) lambda t / N.  Returns (x, z, phi)."""
+    x, z, h = _u64(x), _u64(z), _f64(h)
+    count = N - first if count is None else count
+    idx = qdrift_indices(h, seed, first, count).astype(np.int64)
+    tau = _one_norm(h) * t / N
+    return x[idx].copy(), z[idx].copy(), np.where(h[idx] > 0.0, tau, -tau)
+
+
+def partial_stream(x, z, h, L_D: int, t: float, r: int, Ns: int, seed: int):
+    """The rotations or_partial applies: r steps of delta = t / r, each the
+    terms of H_D in input order with angle delta h_l, then Ns draws from H_R
+    (one SplitMix64 stream through all steps) with angle sgn(h) lambda_R delta / Ns.
+    Returns (x, z, phi)."""
+    x, z, h = _u64(x), _u64(z), _f64(h)
+    is_det = partial_split(h, L_D)
+    det = np.flatnonzero(is_det)
+    rest = np.flatnonzero(~is_det)
+    delta = t / r
+    lam_R = _one_norm(h[rest])
+    sample = rest.size > 0 and Ns > 0 and lam_R > 0.0
+    tau = lam_R * delta / Ns if sample else 0.0
+    xs, zs, ph = [], [], []
+    for step in range(r):
+        xs.append(x[det])
+        zs.append(z[det])
+        ph.append(delta * h[det])
+        if sample:
+            m = qdrift_indices(h[rest], seed, step * Ns, Ns).astype(np.int64)
+            ls = rest[m]
+            xs.append(x[ls])
+            zs.append(z[ls])
+            ph.append(np.where(h[ls] > 0.0, tau, -tau))
+    return np.concatenate(xs), np.concatenate(zs), np.concatenate(ph)

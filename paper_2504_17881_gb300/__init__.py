@@ -20,7 +20,7 @@ from ._lib import (PS_C64, PS_C128, PS_ERR_ARG, PS_ERR_TIMEOUT, PsError, ps_abi_
                    ps_batch_get_info, ps_batch_destroy, ps_batch_describe, ps_ham_trotter_bound, ps_ham_features,
                    ps_ham_error_coefficient,
                    ps_trotter_stream, ps_trotter_sweep, PS_MLP_FEATURES, ps_mlp_create, ps_mlp_destroy,
-                   ps_mlp_num_params, ps_mlp_get_params, ps_mlp_set_params, ps_mlp_get_grads,
+                   ps_mlp_num_params, ps_mlp_get_params, ps_mlp_set_params, ps_mlp_get_grads, ps_mlp_set_grads,
                    ps_mlp_set_normalization, ps_mlp_get_normalization, ps_mlp_fit_normalization, ps_mlp_loss_grad,
                    ps_mlp_adam_step, ps_mlp_train, ps_mlp_predict, ps_mlp_pick_r,
                    ps_mlp_pick_r_ensemble, ps_evolve_trotter2, ps_evolve_partial2, ps_trotter2_length,

@@ -153,6 +153,7 @@ _SIGS = {
     "ps_mlp_get_params": (_i, [_vp, _vp]),
     "ps_mlp_set_params": (_i, [_vp, _vp]),
     "ps_mlp_get_grads": (_i, [_vp, _vp]),
+    "ps_mlp_set_grads": (_i, [_vp, _vp]),
     "ps_mlp_set_normalization": (_i, [_vp, _vp, _vp, ctypes.c_float, ctypes.c_float]),
     "ps_mlp_get_normalization": (_i, [_vp, _vp, _vp, _vp, _vp]),
     "ps_mlp_fit_normalization": (_i, [_vp, _vp, _vp, _sz]),
@@ -603,6 +604,11 @@ def ps_mlp_get_grads(m: int) -> np.ndarray:
     out = np.zeros(ps_mlp_num_params(m), dtype=np.float32)
     _check(lib.ps_mlp_get_grads(ctypes.c_void_p(m), _ptr(out)))
     return out
+
+
+def ps_mlp_set_grads(m: int, g):
+    g = np.ascontiguousarray(np.asarray(g, np.float32))
+    _check(lib.ps_mlp_set_grads(ctypes.c_void_p(m), _ptr(g)))
 
 
 def ps_mlp_set_normalization(m: int, mu, sigma, y_mu: float, y_sigma: float):

@@ -202,6 +202,14 @@ int ps_mlp_get_grads(ps_mlp *m, float *host) {
     return copy_params(m, host, m->G);
 }
 
+int ps_mlp_set_grads(ps_mlp *m, const float *host) {
+    if (!m || !host) return mfail(PS_ERR_ARG, "null argument");
+    Guard g(m->device);
+    cudaError_t e = cudaMemcpyAsync(m->G, host, sizeof(float) * m->nparams, cudaMemcpyHostToDevice, m->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
+    return e != cudaSuccess ? cuda_mfail(e, "ps_mlp_set_grads") : PS_OK;
+}
+
 int ps_mlp_set_params(ps_mlp *m, const float *host) {
     if (!m || !host) return mfail(PS_ERR_ARG, "null argument");
     Guard g(m->device);

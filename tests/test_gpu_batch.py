@@ -33,12 +33,13 @@ def make_runs(ns, seed, rot_lo=200, rot_hi=1500):
     for i, n in enumerate(ns):
         L = int(rng.integers(40, 300)) if n >= 8 else 20
         x, z, h = inputs.jw_hamiltonian(n, L, seed=seed * 1000 + i)
-        H = ps.Hamiltonian(n, x, z, h)
+        # the rotation streams come from the oracle's sampler, so that every
+        # reference the runs are compared with is computed from oracle inputs
         if i % 2 == 0:
-            xs, zs, ph = H.qdrift_stream(0.7, int(rng.integers(rot_lo, rot_hi)), seed + i)
+            xs, zs, ph = oracle.qdrift_stream(x, z, h, 0.7, int(rng.integers(rot_lo, rot_hi)), seed + i)
         else:
             L_D = max(1, L // 10)
-            xs, zs, ph = H.partial_stream(L_D, 0.7, 2, int(rng.integers(rot_lo, rot_hi)) // 2, seed + i)
+            xs, zs, ph = oracle.partial_stream(x, z, h, L_D, 0.7, 2, int(rng.integers(rot_lo, rot_hi)) // 2, seed + i)
         runs.append(dict(n=n, x=xs, z=zs, phi=ph, host0=inputs.gaussian_state(n, seed * 1000 + 500 + i)))
     return runs
 

@@ -92,9 +92,7 @@ ROT28 = 1000
 @pytest.fixture(scope="module")
 def n28_case():
     x, z, h = inputs.jw_hamiltonian(N28, N_TERMS, seed=HAM_SEED)
-    H = ps.Hamiltonian(N28, x, z, h)
-    xs, zs, ph = H.qdrift_stream(T_TOTAL, N_SAMPLES, QDRIFT_SEED, first=0, count=ROT28)
-    H.close()
+    xs, zs, ph = oracle.qdrift_stream(x, z, h, T_TOTAL, N_SAMPLES, QDRIFT_SEED, first=0, count=ROT28)
     psi0 = inputs.gaussian_state(N28, 28)
     ref = psi0.copy()
     tmp = np.empty_like(ref)
@@ -144,9 +142,7 @@ PREFIX30 = 26  # the oracle's single-amplitude evaluation takes at most 26 rotat
 @pytest.fixture(scope="module")
 def n30_case():
     x, z, h = inputs.jw_hamiltonian(N30, N_TERMS, seed=HAM_SEED)
-    H = ps.Hamiltonian(N30, x, z, h)
-    xs, zs, ph = H.qdrift_stream(T_TOTAL, N_SAMPLES, QDRIFT_SEED, first=0, count=PREFIX30)
-    H.close()
+    xs, zs, ph = oracle.qdrift_stream(x, z, h, T_TOTAL, N_SAMPLES, QDRIFT_SEED, first=0, count=PREFIX30)
     assert np.all(xs != 0)
     idx, amp = inputs.determinant_state(N30, seed=11)
     return dict(xs=xs, zs=zs, ph=ph, idx=idx, amp=amp)
@@ -191,9 +187,7 @@ def test_64bit_indices_sampled_amplitudes_vs_oracle(n, dtype):
     benchmark's, so that every flip moves amplitude visibly), at least five
     of them with an X bit on one of the top two qubits; 96 amplitudes."""
     x, z, h = inputs.jw_hamiltonian(n, 2000, seed=60 + n)
-    H = ps.Hamiltonian(n, x, z, h)
-    xs, zs, ph = H.qdrift_stream(10.0 * T_TOTAL, N_SAMPLES, 61 + n, first=0, count=400)
-    H.close()
+    xs, zs, ph = oracle.qdrift_stream(x, z, h, 10.0 * T_TOTAL, N_SAMPLES, 61 + n, first=0, count=400)
     top = (1 << (n - 1)) | (1 << (n - 2))
     hi = np.flatnonzero((xs & np.uint64(top)) != 0)[:5]
     lo = np.flatnonzero((xs & np.uint64(top)) == 0)[:15]

@@ -148,7 +148,7 @@ def test_fused_equals_rotation_by_rotation(dtype):
     n = 20
     xh, zh, hh = inputs.jw_hamiltonian(n, 500, seed=7)
     H = ps.Hamiltonian(n, xh, zh, hh)
-    x, z, phi = H.qdrift_stream(1.0, 400, 8)
+    x, z, phi = oracle.qdrift_stream(xh, zh, hh, 1.0, 400, 8)
     psi0 = inputs.gaussian_state(n, 6)
     fused, _, _ = run_rotations(n, dtype, psi0, x, z, phi)
     unfused, _, _ = run_rotations(n, dtype, psi0, x, z, phi, {"max_window": 1})
@@ -168,7 +168,7 @@ def test_segment_sizes_and_group_shapes_vs_oracle(dtype, tuning):
     n = 18
     xh, zh, hh = inputs.jw_hamiltonian(n, 400, seed=17)
     H = ps.Hamiltonian(n, xh, zh, hh)
-    x, z, phi = H.qdrift_stream(1.0, 500, 18)
+    x, z, phi = oracle.qdrift_stream(xh, zh, hh, 1.0, 500, 18)
     psi0 = inputs.gaussian_state(n, 19)
     ref = oracle.apply(psi0, x, z, phi)
     if dtype == ps.PS_C128 and tuning.get("group_bits") == 5:
@@ -193,7 +193,7 @@ def test_tile_threads_give_the_same_amplitudes(dtype, tuning):
     n = 22
     xh, zh, hh = inputs.jw_hamiltonian(n, 300, seed=23)
     H = ps.Hamiltonian(n, xh, zh, hh)
-    x, z, phi = H.qdrift_stream(1.0, 160, 24)
+    x, z, phi = oracle.qdrift_stream(xh, zh, hh, 1.0, 160, 24)
     psi0 = inputs.gaussian_state(n, 25)
     if dtype == ps.PS_C128:
         tuning = dict(tuning, reg_groups=min(tuning.get("reg_groups", 1), 2))
@@ -229,7 +229,7 @@ def test_complex64_norm_does_not_drift_over_long_small_angle_runs():
     xh, zh, hh = inputs.jw_hamiltonian(n, 500, seed=9)
     H = ps.Hamiltonian(n, xh, zh, hh)
     N = 100_000
-    x, z, phi = H.qdrift_stream(10.0, N, 10)
+    x, z, phi = oracle.qdrift_stream(xh, zh, hh, 10.0, N, 10)
     assert np.max(np.abs(phi)) > 1e-4
     psi0 = inputs.gaussian_state(n, 11)
     s64 = gpu_state(n, ps.PS_C64, psi0)
@@ -249,7 +249,7 @@ def test_represented_state_applies_the_carried_scale():
     n = 12
     xh, zh, hh = inputs.jw_hamiltonian(n, 200, seed=41)
     H = ps.Hamiltonian(n, xh, zh, hh)
-    x, z, phi = H.qdrift_stream(20.0, 20_000, 42)
+    x, z, phi = oracle.qdrift_stream(xh, zh, hh, 20.0, 20_000, 42)
     psi0 = inputs.gaussian_state(n, 43)
     st = gpu_state(n, ps.PS_C64, psi0)
     st.apply_rotations(x[:19_999], z[:19_999], phi[:19_999])
@@ -375,8 +375,8 @@ def ham30():
 
 def test_n30_forward_then_inverse_returns_initial_state(ham30):
     """P^2 = I makes the reversed sequence with negated angles the exact inverse."""
-    _, _, _, H = ham30
-    xs, zs, ph = H.qdrift_stream(1.0, 100_000, 4, first=0, count=3000)
+    xh, zh, hh, _ = ham30
+    xs, zs, ph = oracle.qdrift_stream(xh, zh, hh, 1.0, 100_000, 4, first=0, count=3000)
     idx, amp = inputs.determinant_state(N30, seed=11)
     st = ps.StateVector(N30, dtype=torch.complex64)
     st.tensor.zero_()

@@ -461,3 +461,20 @@ def test_threaded_oracle_gives_the_same_rotations():
     assert np.array_equal(one, many)
     assert np.array_equal(a1, a4)
     assert abs(g1 - g4) < 1e-14 and abs(n1 - n4) < 1e-14
+
+
+def test_oracle_streams_are_the_rotations_its_drivers_apply():
+    """qdrift_stream / partial_stream list exactly the rotations or_qdrift and
+    or_partial apply: applying the listed rotations gives bitwise the same
+    state (same angles, same order, same products)."""
+    n = 7
+    x, z, h = inputs.jw_hamiltonian(n, 50, seed=61)
+    psi0 = inputs.gaussian_state(n, 62)
+    xs, zs, ph = oracle.qdrift_stream(x, z, h, 0.9, 120, 63)
+    assert np.array_equal(oracle.apply(psi0, xs, zs, ph), oracle.qdrift(psi0, x, z, h, 0.9, 120, 63))
+    a, b, c = oracle.qdrift_stream(x, z, h, 0.9, 120, 63, first=40, count=30)
+    assert np.array_equal(a, xs[40:70]) and np.array_equal(b, zs[40:70]) and np.array_equal(c, ph[40:70])
+    for L_D, Ns in ((10, 7), (0, 9), (50, 5)):
+        xs, zs, ph = oracle.partial_stream(x, z, h, L_D, 0.8, 3, Ns, 64)
+        assert len(ph) == 3 * (L_D + (Ns if L_D < 50 else 0))
+        assert np.array_equal(oracle.apply(psi0, xs, zs, ph), oracle.partial(psi0, x, z, h, L_D, 0.8, 3, Ns, 64))

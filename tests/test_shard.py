@@ -244,7 +244,7 @@ def test_ranks_emulated_on_one_gpu_with_libps(dtype, tol):
     n, m = 16, 3
     s = n - m
     x, z, h = inputs.jw_hamiltonian(n, 200, seed=51)
-    xs, zs, ph = ps.Hamiltonian(n, x, z, h).qdrift_stream(0.8, 400, 5)
+    xs, zs, ph = oracle.qdrift_stream(x, z, h, 0.8, 400, 5)
     psi = inputs.gaussian_state(n, 52)
     pdt = ps.PS_C64 if dtype == torch.complex64 else ps.PS_C128
     pack, unpack = shard.libps_moves(s, pdt)
