@@ -79,6 +79,9 @@ def parse():
     ap.add_argument("--no-sequential", action="store_true", help="batched: skip the one-run-at-a-time comparison")
     ap.add_argument("--no-autotune", action="store_true", help="batched: default lane size and tile bits")
     ap.add_argument("--train-problems", type=int, default=128, help="learned: training Hamiltonians")
+    ap.add_argument("--train-times", type=int, choices=[8, 16], default=8,
+                    help="learned: times per Hamiltonian (8: every second of the 16 of the configuration)")
+    ap.add_argument("--train-nmax", type=int, default=18, help="learned: largest n of the training Hamiltonians")
     ap.add_argument("--use-qubits", type=int, default=32, help="learned: qubits of the step-choice queries")
     ap.add_argument("--qubits", type=int, default=30,
                     help="state size; values other than 30 are for profiling captures only")
@@ -682,16 +685,16 @@ def run_learned(args):
     eps = 1e-3
     P = args.train_problems
     t0 = time.perf_counter()
-    probs = learned.synthetic_problems(P, seed=1000, n_range=(14, 18), L_range=(200, 2000), lam_range=(1.0, 10.0),
-                                       far_every=2)
-    times = learned.TIMES16[::2]
+    probs = learned.synthetic_problems(P, seed=1000, n_range=(14, args.train_nmax), L_range=(200, 2000),
+                                       lam_range=(1.0, 10.0), far_every=2)
+    times = learned.TIMES16 if args.train_times == 16 else learned.TIMES16[::2]
     torch.cuda.synchronize()
     tg = time.perf_counter()
     X, y, info = learned.training_rows(probs, times=times)
     torch.cuda.synchronize()
     gen_s = time.perf_counter() - tg
     gen_rot = sum(probs[pi].L * r for pi in range(P) for _ in times for r in (1, 2, 4, 8, 16, 32, 64, 128))
-    hold = 16
+    hold = max(16, P // 10)  # Hamiltonians held out for the pick margin
     cut = (P - hold) * len(times) * len(learned.R_VALUES)
     m = learned.StepEnsemble(count=4, seed=2)
     tt = time.perf_counter()
@@ -744,8 +747,10 @@ def run_learned(args):
                   f"(n={n} complex64, eps=1e-3)",
         "value": tot_sw / max(1, tot_ml), "unit": "x", "n_gpus": 1, "higher_is_better": True, "data": "synthetic",
         "dtype": "f32 network, c128 training data, c64 use",
-        "config": {"workload": f"train: {P} JW-like H (n 14..18, 200-2000 terms, one-norm 1..10; every 2nd guiding state "
-                               f"with determinants >= 10 flips apart), {len(times)} times 0.1..2.5, r 1..64; use: n={n}, 1000 terms, one-norm 8, 8-determinant state",
+        "config": {"workload": f"train: {P} JW-like H (n 14..{args.train_nmax}, 200-2000 terms, one-norm 1..10; every 2nd "
+                               f"guiding state with determinants >= 10 flips apart), {len(times)} times "
+                               f"{times[0]:.1f}..{times[-1]:.1f}, r 1..64; use: n={n}, 1000 terms, one-norm 8, "
+                               f"8-determinant state, {len(LEARNED_TIMES)} times",
                    "training_rows": int(cut), "held_out_rows": int(len(pv)),
                    "network": "4 x (12 -> 128 -> 128 -> 128 -> 1, tanh, FP32, Adam), mean of log errors"},
         "training": {"data_generation_s": gen_s, "data_rotations": gen_rot, "train_s": train_s,

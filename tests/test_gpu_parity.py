@@ -236,7 +236,10 @@ def test_complex64_norm_does_not_drift_over_long_small_angle_runs():
     s128 = gpu_state(n, ps.PS_C128, psi0)
     s64.apply_rotations(x, z, phi)
     s128.apply_rotations(x, z, phi)
-    assert abs(s128.norm2() - 1.0) < 1e-12
+    # FP64: every rotation has the same |angle|, so the rounding of tan(phi) and
+    # cos(phi) biases the norm the same way each time, up to 4 * 2^-53 per
+    # rotation (4e-18 here), plus one rounding per carried-factor update
+    assert abs(s128.norm2() - 1.0) < N * 4 * 2.0 ** -53
     assert abs(s64.norm2() - 1.0) < 2e-5
     # random-walk rounding error only: sqrt(N) * ~1e-7
     assert rel(represented(s64), represented(s128)) < 1e-4
@@ -266,6 +269,28 @@ def test_represented_state_applies_the_carried_scale():
     assert rel(rep, ref) < 1e-4
     if abs(f - 1.0) > 1e-6:
         assert rel(rep, ref) < rel(stored.astype(np.complex128), ref)
+
+
+def test_complex128_carried_scale_stays_within_its_band():
+    """complex128 applies the carried cos(phi) factor only once it leaves
+    |f - 1| <= 2^-20: in between the stored amplitudes are the state divided by
+    f, and every readout (represented state, norm, overlap) includes it."""
+    n = 11
+    xh, zh, hh = inputs.jw_hamiltonian(n, 150, seed=44)
+    x, z, phi = oracle.qdrift_stream(xh, zh, hh, 0.3, 3000, 45)  # |phi| ~ 1e-4: the factor builds up over many passes
+    psi0 = inputs.gaussian_state(n, 46)
+    st = gpu_state(n, ps.PS_C128, psi0)
+    seen = set()
+    for lo in range(0, 3000, 300):
+        st.apply_rotations(x[lo:lo + 300], z[lo:lo + 300], phi[lo:lo + 300])
+        f = st.scale()
+        assert abs(f - 1.0) <= 2.0 ** -20
+        seen.add(f != 1.0)
+    assert True in seen  # the factor was carried at least once
+    ref = oracle.apply(psi0, x, z, phi)
+    assert rel(st.to_numpy(), ref) < 1e-12
+    assert abs(st.norm2() - 1.0) < 1e-12
+    assert rel_scalar(st.overlap(gpu_state(n, ps.PS_C128, psi0)), oracle.overlap(psi0, ref)) < 1e-12
 
 
 @pytest.mark.parametrize("dtype", [ps.PS_C128, ps.PS_C64])
