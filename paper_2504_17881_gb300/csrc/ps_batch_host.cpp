@@ -193,10 +193,7 @@ int build_layout(int dtype, const ps_run_desc *runs, size_t nruns, const BatchCf
             pending *= w.kprod;
             const double dev = pending - 1.0;
             double kd = 0.0;
-            if (wi + 1 == p.win.size() || dtype == PS_C128)
-                kd = dev;
-            else if (std::fabs(dev) > 0x1.0p-16)
-                kd = dev;
+            if (wi + 1 == p.win.size() || std::fabs(dev) > (dtype == PS_C128 ? 0x1.0p-20 : 0x1.0p-16)) kd = dev;
             if (dtype == PS_C64) kd = (double)(float)kd;
             if (kd != 0.0) pending /= (1.0 + kd);
             bw.kdelta = kd;
