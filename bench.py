@@ -78,6 +78,10 @@ def parse():
     ap.add_argument("--batch-runs", type=int, default=BATCH_RUNS)
     ap.add_argument("--no-sequential", action="store_true", help="batched: skip the one-run-at-a-time comparison")
     ap.add_argument("--no-autotune", action="store_true", help="batched: default lane size and tile bits")
+    ap.add_argument("--no-c128", action="store_true", help="batched: skip the complex128 comparison batch")
+    ap.add_argument("--batch-n", type=int, default=None, help="batched: every run at this n (default 14..22)")
+    ap.add_argument("--batch-rotations", type=int, default=None,
+                    help="batched: every run with this many rotations (default 2000..20000)")
     ap.add_argument("--train-problems", type=int, default=128, help="learned: training Hamiltonians")
     ap.add_argument("--train-times", type=int, choices=[8, 16], default=8,
                     help="learned: times per Hamiltonian (8: every second of the 16 of the configuration)")
@@ -492,10 +496,11 @@ def run_e2e(ps, torch, dev, segs, idx, amp, steps):
 
 # ---------------------------------------------------------------- batched
 
-def batched_workload(nruns: int, seed: int = BATCH_SEED):
+def batched_workload(nruns: int, seed: int = BATCH_SEED, n_fixed: int | None = None, rot_fixed: int | None = None):
     """Independent runs of uneven size: n uniform in 14..22, 200-2000 JW-like
     terms per Hamiltonian, 2000-20000 rotations; even runs qDRIFT, odd runs
-    partially randomised (L_D = 10% of the terms, r = 4 steps)."""
+    partially randomised (L_D = 10% of the terms, r = 4 steps).  n_fixed /
+    rot_fixed give every run that n / rotation count (profiling workloads)."""
     import paper_2504_17881_gb300 as ps
     from paper_2504_17881_gb300 import inputs
     rng = np.random.default_rng(seed)
@@ -504,6 +509,8 @@ def batched_workload(nruns: int, seed: int = BATCH_SEED):
         n = int(rng.integers(14, 23))
         L = int(rng.integers(200, 2001))
         cnt = int(rng.integers(2000, 20001))
+        n = n_fixed if n_fixed else n
+        cnt = rot_fixed if rot_fixed else cnt
         x, z, h = inputs.jw_hamiltonian(n, L, seed=seed * 100000 + i)
         H = ps.Hamiltonian(n, x, z, h)
         if i % 2 == 0:
@@ -532,7 +539,7 @@ def run_batched(args):
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
     t_host = time.perf_counter()
-    runs = batched_workload(args.batch_runs, BATCH_SEED + 1000 * rank)
+    runs = batched_workload(args.batch_runs, BATCH_SEED + 1000 * rank, args.batch_n, args.batch_rotations)
     host_gen_s = time.perf_counter() - t_host
 
     def psi0_for(r, dtype):
@@ -603,13 +610,13 @@ def run_batched(args):
             torch.cuda.synchronize(dev)
         seq_ms = e0.elapsed_time(e1)
         seq = {"ms": seq_ms, "value": rot_per_launch / (seq_ms / 1e3), "unit": UNIT,
-               "how": "512 x (copy psi0, ps_plan_apply of the run's prebuilt plan, ps_overlap), default tuning",
+               "how": f"{len(runs)} x (copy psi0, ps_plan_apply of the run's prebuilt plan, ps_overlap), default tuning",
                "speedup_batch_vs_sequential": seq_ms / (ms / args.steps)}
         del plans, svs
 
     # complex64 vs complex128 (the batch engine in FP64 on the same runs)
     c128 = None
-    if world == 1:
+    if world == 1 and not args.no_c128:
         runs128 = [dict(r, psi0=psi0_for(r, torch.complex128), state=None) for r in runs]
         for r in runs:
             r.pop("psi0", None)
@@ -642,9 +649,10 @@ def run_batched(args):
         "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": t_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"{len(runs)} runs, n uniform 14..22 (mean state {np.mean([8 << n for n in ns]) / 2**20:.1f} MiB), "
-                               "200-2000 JW-like terms, 2000-20000 rotations, half qDRIFT half partial (L_D 10%, r 4), "
-                               "8-determinant psi0 per run",
+        "config": {"workload": f"{len(runs)} runs, n {f'= {args.batch_n}' if args.batch_n else 'uniform 14..22'} "
+                               f"(mean state {np.mean([8 << n for n in ns]) / 2**20:.1f} MiB), 200-2000 JW-like terms, "
+                               f"{args.batch_rotations or '2000-20000'} rotations, half qDRIFT half partial "
+                               "(L_D 10%, r 4), 8-determinant psi0 per run",
                    "runs": len(runs), "rotations_per_step": rot_per_launch,
                    "l2": f"{sum(8 << n for n in ns) / 2**30:.2f} GiB of states per step (> 129 MB L2), no flush",
                    "batch": {k: info[k] for k in ("grid", "ctas_per_sm", "lanes", "lane_size", "tile_bits",

@@ -193,7 +193,7 @@ struct Cursor {
 
 // Advance the cursor to the next item of the CTA (thread 0 only; lane
 // barriers wait here while the other threads wait at the CTA barrier).
-template <int G, int NG>
+template <int G, int NG, int LGT>
 __device__ void next_item(const BatchArgs &A, Cursor &cu, Item &it) {
     for (;;) {
         if (cu.phase == 2) {
@@ -261,8 +261,8 @@ __device__ void next_item(const BatchArgs &A, Cursor &cu, Item &it) {
         }
         case 2: {  // this CTA's tiles of the window, all in one item
             const bool resident = cu.kind == -2;
-            // a full block of register groups: 2^(B - G) / NG >= kBatchThreads
-            const bool full = !resident && cu.B - G - (NG == 4 ? 2 : NG == 2 ? 1 : 0) >= 8;
+            // a full block of register groups: 2^(B - G) / NG >= 2^LGT threads
+            const bool full = !resident && cu.B - G - (NG == 4 ? 2 : NG == 2 ? 1 : 0) >= LGT;
             it.op = full ? kOpTile : kOpTileGen;
             it.h = cu.h;
             it.hstep = cu.phase == 0 ? (uint32_t)cu.S : 1u;
@@ -336,8 +336,10 @@ __device__ void next_item(const BatchArgs &A, Cursor &cu, Item &it) {
 // shared cursor), so each pass has the single-window kernel's register
 // budget to itself.
 template <typename R, int G, int NG>
-__global__ void __launch_bounds__(kBatchThreads, tile_min_blocks<R, G, NG>()) k_batch(const __grid_constant__ BatchArgs A) {
+__global__ void __launch_bounds__(batch_threads<R>(), 3) k_batch(const __grid_constant__ BatchArgs A) {
     using C = typename CT<R>::T;
+    constexpr int LGT = batch_threads<R>() == 128 ? 7 : 8;
+    static_assert(batch_threads<R>() == (1 << LGT), "128 or 256 threads");
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ Cursor cu;
     __shared__ Item it;
@@ -358,7 +360,7 @@ __global__ void __launch_bounds__(kBatchThreads, tile_min_blocks<R, G, NG>()) k_
     }
     for (;;) {
         __syncthreads();
-        if (threadIdx.x == 0) next_item<G, NG>(A, cu, it);
+        if (threadIdx.x == 0) next_item<G, NG, LGT>(A, cu, it);
         __syncthreads();
         const int op = it.op;
         if (op == kOpDone) break;
@@ -406,7 +408,7 @@ __global__ void __launch_bounds__(kBatchThreads, tile_min_blocks<R, G, NG>()) k_
 
 template <typename R>
 void *batch_kernel() {
-    return reinterpret_cast<void *>(&k_batch<R, kBatchG, 2>);
+    return reinterpret_cast<void *>(&k_batch<R, kBatchG, kBatchNG>);
 }
 
 }  // namespace
@@ -417,7 +419,8 @@ int batch_occupancy(int dtype, size_t smem_bytes, int *blocks_per_sm) {
     constexpr int kBatchSmemLimit = 200 * 1024;
     if (smem_bytes > (size_t)kBatchSmemLimit) return (int)cudaErrorInvalidValue;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, kBatchSmemLimit);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, kBatchThreads, smem_bytes);
+    const int threads = dtype == PS_C64 ? batch_threads<float>() : batch_threads<double>();
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, threads, smem_bytes);
     return (int)e;
 }
 
@@ -425,7 +428,7 @@ int launch_batch(int dtype, const BatchArgs &a, int grid, size_t smem_bytes, voi
     void *fn = dtype == PS_C64 ? batch_kernel<float>() : batch_kernel<double>();
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)grid);
-    cfg.blockDim = dim3(kBatchThreads);
+    cfg.blockDim = dim3((unsigned)(dtype == PS_C64 ? batch_threads<float>() : batch_threads<double>()));
     cfg.dynamicSmemBytes = smem_bytes;
     cfg.stream = (cudaStream_t)stream;
     cudaLaunchAttribute attr[1];

@@ -185,12 +185,19 @@ struct BatchArgs {
 // Resident CTAs per SM of the batched kernel with this dynamic shared memory
 // (also raises the kernel's dynamic shared-memory limit to it).
 int batch_occupancy(int dtype, size_t smem_bytes, int *blocks_per_sm);
-// Cooperative launch of the batched kernel (kTileThreads threads per CTA).
+// Cooperative launch of the batched kernel (batch_threads<R>() threads per CTA).
 int launch_batch(int dtype, const BatchArgs &a, int grid, size_t smem_bytes, void *stream);
-constexpr int kBatchThreads = 256;
 // Bytes of one per-rotation record in a tile pass's shared memory (KRot).
 constexpr size_t kRecBytesC64 = 160, kRecBytesC128 = 288;
 constexpr int kBatchG = 3;       // group bits of the batched kernel
+constexpr int kBatchNG = 2;      // register groups of 2^kBatchG amplitudes per thread
+// Threads per CTA of the batched kernel, sized for three CTAs per SM: 256
+// complex64 threads of 16 amplitudes (up to 80 registers each), 128
+// complex128 threads of 16 amplitudes (up to 168).  Measured on the 512-run
+// workload: 128 complex64 threads of 32 amplitudes were 1.4% slower, and 128
+// complex128 threads were 4.6% faster than 256 at 128 registers.
+template <typename R>
+__host__ __device__ constexpr int batch_threads() { return sizeof(R) == 4 ? 256 : 128; }
 constexpr int kLaneStrideWords = 32;
 
 // ------------------------------------------------------ learned step choice

@@ -197,13 +197,6 @@ __device__ __forceinline__ uint64_t v_of(const TileParams &P, uint32_t x) {
 // spread a thread's fixed work per round (descriptor decoding, coset
 // representatives, address bases) over more amplitudes.
 constexpr int tile_max_threads(int real_bytes, int G, int NG) { return (NG << G) * real_bytes <= 64 ? 256 : 128; }
-// Resident CTAs per SM the batched kernel's register budget is sized for:
-// three when a thread holds at most 16 complex64 (8 complex128) amplitudes,
-// else two.
-template <typename R, int G, int NG>
-constexpr int tile_min_blocks() {
-    return (NG << G) * (int)sizeof(R) <= 64 ? 3 : 2;
-}
 
 // Per-window tables of a CTA, one copy for every instance of the pass:
 // V over each 4-bit nibble of a segment index, and the global offsets W_i of
