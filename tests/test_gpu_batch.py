@@ -77,6 +77,20 @@ def test_batch_matches_single_runs(dtype):
         assert abs(g[i] - g_ref) < TOL[dtype] * max(1.0, abs(g_ref)), (i, g[i], g_ref)
 
 
+@pytest.mark.parametrize("dtype", [ps.PS_C128, ps.PS_C64])
+def test_batch_smallest_states_vs_oracle(dtype):
+    # n = 4 and 5: tiles smaller than one thread's register groups leave most
+    # of the CTA without rotation work (one or two active threads)
+    runs = make_runs([4, 5, 4, 5, 7], seed=41, rot_lo=50, rot_hi=200)
+    b = ps.Batch(device_runs(runs, dtype), dtype=TDT[dtype], cfg=dict(lane_size=8))
+    g = b.run()
+    for i, r in enumerate(runs):
+        ref = oracle.apply(r["host0"], r["x"], r["z"], r["phi"])
+        assert rel(b.states[i].cpu().numpy(), ref) < TOL[dtype], (i, r["n"])
+        g_ref = oracle.overlap(r["host0"], ref)
+        assert abs(g[i] - g_ref) < TOL[dtype] * max(1.0, abs(g_ref)), (i, g[i], g_ref)
+
+
 def test_batch_complex128_vs_oracle():
     runs = make_runs([8, 11, 13, 14, 16], seed=5, rot_lo=100, rot_hi=300)
     b = ps.Batch(device_runs(runs, ps.PS_C128), dtype=torch.complex128, cfg=dict(lane_size=4))
