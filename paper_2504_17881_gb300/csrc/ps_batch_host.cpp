@@ -149,7 +149,7 @@ int build_layout(int dtype, const ps_run_desc *runs, size_t nruns, const BatchCf
             Tuning t{};
             t.B = std::max(6, run_tile_bits(r.n, kind[i], cfg));
             t.G = kBatchG;
-            t.max_window = kParamRot;
+            t.max_window = batch_max_window(dtype);
             t.pair_single = 2;
             t.kernel_timing = 0;
             t.reg_groups = 2;
@@ -199,7 +199,7 @@ int build_layout(int dtype, const ps_run_desc *runs, size_t nruns, const BatchCf
             bw.kdelta = kd;
             pack_window(p, w, L.bodies);
             L.wins.push_back(bw);
-            L.smem = std::max(L.smem, (amp_bytes(dtype) << bw.B) + (size_t)kParamRot * rec);
+            L.smem = std::max(L.smem, (amp_bytes(dtype) << bw.B) + (size_t)batch_max_window(dtype) * rec);
         }
         const double N = std::ldexp(1.0, br.n);
         L.work[i] = N * (double)(br.nwin + 1);
@@ -209,14 +209,14 @@ int build_layout(int dtype, const ps_run_desc *runs, size_t nruns, const BatchCf
         inf.amplitude_rotations += N * (double)runs[i].count;
         if (kind[i] == -2) {
             inf.resident_runs++;
-            L.smem = std::max(L.smem, (amp_bytes(dtype) << br.n) + (size_t)kParamRot * rec);
+            L.smem = std::max(L.smem, (amp_bytes(dtype) << br.n) + (size_t)batch_max_window(dtype) * rec);
         } else if (kind[i] == -1) {
             inf.single_runs++;
         } else {
             inf.lane_runs++;
         }
     }
-    if (L.smem == 0) L.smem = (amp_bytes(dtype) << 4) + (size_t)kParamRot * rec;
+    if (L.smem == 0) L.smem = (amp_bytes(dtype) << 4) + (size_t)batch_max_window(dtype) * rec;
 
     // lanes: longest first onto the least-loaded lane; each lane then runs
     // its runs longest first
@@ -351,7 +351,7 @@ int ps_batch_create(int dtype, const ps_run_desc *runs, size_t nruns, const ps_b
                 max_other = std::max(max_other, std::min(runs[i].n, c.tile_bits));
         }
     const size_t smem = (amp_bytes(dtype) << std::max(4, std::max(max_res, max_other))) +
-                        (size_t)kParamRot * (dtype == PS_C64 ? kRecBytesC64 : kRecBytesC128);
+                        (size_t)batch_max_window(dtype) * (dtype == PS_C64 ? kRecBytesC64 : kRecBytesC128);
     e = (cudaError_t)batch_occupancy(dtype, smem, &occ);
     if (e != cudaSuccess) return cuda_bfail(e, "ps_batch_create: occupancy");
     if (occ < 1) return bfail(PS_ERR_UNSUPPORTED, "batched kernel does not fit on an SM with this shared memory");

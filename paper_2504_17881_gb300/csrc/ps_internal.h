@@ -191,6 +191,11 @@ int launch_batch(int dtype, const BatchArgs &a, int grid, size_t smem_bytes, voi
 constexpr size_t kRecBytesC64 = 160, kRecBytesC128 = 288;
 constexpr int kBatchG = 3;       // group bits of the batched kernel
 constexpr int kBatchNG = 2;      // register groups of 2^kBatchG amplitudes per thread
+// Most rotations of a batched window.  Every CTA of a batch reserves records
+// for this many rotations next to its tile, so three complex128 CTAs of a
+// 2^12-amplitude tile (64 KB) fit the SM's 228 KB only with at most 25
+// 288-byte records each (24 kept, with room for the static shared memory).
+inline int batch_max_window(int dtype) { return dtype == PS_C64 ? kParamRot : 24; }
 // Threads per CTA of the batched kernel, sized for three CTAs per SM: 256
 // complex64 threads of 16 amplitudes (up to 80 registers each), 128
 // complex128 threads of 16 amplitudes (up to 168).  Measured on the 512-run

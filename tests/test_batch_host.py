@@ -49,7 +49,8 @@ def test_windows_equal_single_run_schedule(dtype):
     amp = 0.0
     for r, tb, nw in zip(runs, d["tile_bits_of"], d["windows_of"]):
         info = ps.ps_plan_describe(r["n"], dtype, r["x"], r["z"], r["phi"],
-                                   dict(tile_bits=max(6, int(tb)), group_bits=3, max_window=32, pair_single=2))
+                                   dict(tile_bits=max(6, int(tb)), group_bits=3,
+                                        max_window=32 if dtype == ps.PS_C64 else 24, pair_single=2))
         assert info["windows"] == nw and info["pair_windows"] == 0
         tot += int(nw)
         amp += float(2 ** r["n"]) * int(nw)

@@ -4,9 +4,9 @@ Every run of a batch must give the state and overlap that the same rotation
 list gives on its own (ps_apply_rotations on a state handle), which the
 single-run tests tie to the oracle; small complex128 runs are also compared
 with the oracle directly.  The batch uses its own windows (other tile bits,
-at most 32 rotations each), so the complex64 comparison allows the rounding
-of two different schedules: 2e-5 relative L2 for up to ~2000 rotations
-(sqrt(m) * 1e-7 per schedule, twice).
+at most 32 complex64 or 24 complex128 rotations each), so the complex64
+comparison allows the rounding of two different schedules: 2e-5 relative L2
+for up to ~2000 rotations (sqrt(m) * 1e-7 per schedule, twice).
 """
 import numpy as np
 import pytest
