@@ -152,7 +152,7 @@ int build_layout(int dtype, const ps_run_desc *runs, size_t nruns, const BatchCf
             t.max_window = batch_max_window(dtype);
             t.pair_single = 2;
             t.kernel_timing = 0;
-            t.reg_groups = 2;
+            t.reg_groups = kBatchNG;  // recorded in the plan; the batched kernel fixes its own
             t.seg_bits = dtype == PS_C64 ? 4 : 3;
             t.tile_threads = 0;
             rc[i] = build_plan(r.n, dtype, r.x, r.z, r.phi, r.count, t, plans[i], &errs[i]);
