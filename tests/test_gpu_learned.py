@@ -219,12 +219,12 @@ def test_learned_pick_gains_over_sweep(trained):
     for row in rows:
         print(f"{row[0]:4.0f} {row[1]:6.0f} {row[3]:8.0f} {row[7]:6.0f}   {row[5]:.2e}      {row[6]:.2e}")
     print(f"rotations: learned {rot_ml.sum():.0f}, sweep {rot_sw.sum():.0f} ({rot_ml.sum() / rot_sw.sum():.2f})")
-    # the learned r is within a factor 3 of the smallest adequate one (the
-    # calibrated margin makes it err on the safe side) ...
-    assert np.mean(np.abs(np.log2(r_ml / r_star)) <= math.log2(3.0) + 1e-9) >= 0.75
-    # ... meets the target within a factor 2 in most cases, never far off
-    assert np.mean(err_ml <= 2 * eps) >= 0.75 and err_ml.max() <= 6 * eps
+    # the learned r is within a factor 3 of the smallest adequate one in
+    # every case (the calibrated margin makes it err on the safe side) ...
+    assert np.all(np.abs(np.log2(r_ml / r_star)) <= math.log2(3.0) + 1e-9)
+    # ... meets the target in most cases and is never off by more than 2x
+    assert np.mean(err_ml <= eps) >= 0.7 and err_ml.max() <= 2 * eps
     # and costs far fewer rotations than the sweep (which runs 1, 2, 4, ..., 2 r_sw)
-    assert rot_ml.sum() < 0.5 * rot_sw.sum()
+    assert rot_ml.sum() < 0.35 * rot_sw.sum()
     # the analytic bound asks for many more steps than needed
     assert np.median(r_bd / r_star) > 3
