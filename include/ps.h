@@ -492,6 +492,8 @@ typedef struct ps_batch_info {
 
 /* Schedule every run (host, in parallel threads), upload the windows and
  * prepare the launch on `stream` (a cudaStream_t; the current device).
+ * A batched window holds at most 32 (PS_C64) or 24 (PS_C128) rotations, so
+ * that three CTAs with their tiles and per-rotation records share an SM.
  * Fails with PS_ERR_ARG on an invalid run (n outside 4..30, null or
  * misaligned buffers, a state shared by two runs or aliasing a psi0, a mask
  * bit >= n, a non-finite angle) or configuration, PS_ERR_OOM when device
