@@ -237,7 +237,26 @@ __device__ __forceinline__ void issue_tile_loads(const typename CT<R>::T *src, u
         // Gray steps 1, 2, 1 of every group of four iterations use v[it_shift]
         // and v[it_shift + 1] from registers; only the fourth reads the window
         const uint64_t va = niter > 1 ? P.v[it_shift] : 0, vb = niter > 2 ? P.v[it_shift + 1] : 0;
-        if (n <= 32) {
+        if (n <= 32 && niter >= 8) {
+            // amplitude indices fit 32 bits.  Chunk set g = 8 q + j: the high
+            // part q in Gray order (one table read per eight copies), the low
+            // three bits j in order from eight precomputed V(j), so a copy
+            // costs one XOR, one wide multiply-add and one add for its
+            // shared-memory address.
+            const char *gb = gbase + off;
+            const uint32_t va32 = (uint32_t)va, vb32 = (uint32_t)vb, vc32 = (uint32_t)P.v[it_shift + 2];
+            const uint32_t vj[8] = {0u, va32, vb32, va32 ^ vb32, vc32, vc32 ^ va32, vc32 ^ vb32, vc32 ^ vb32 ^ va32};
+            const uint32_t sstep = 16u << lgB;
+            uint32_t bq = (uint32_t)base;
+            for (int q = 0; q < (niter >> 3); ++q) {
+                if (q) bq ^= (uint32_t)P.v[it_shift + 3 + (__ffs(q) - 1)];
+                const uint32_t gq = (uint32_t)(q ^ (q >> 1)) << 3;
+                unsigned char *sb = buf + (size_t)tid * 16 + (size_t)gq * sstep;
+#pragma unroll
+                for (int j = 0; j < 8; ++j)
+                    cp_async16(sb + (size_t)j * sstep, gb + (uint64_t)(bq ^ vj[j]) * (1u << LS));
+            }
+        } else if (n <= 32) {
             // amplitude indices fit 32 bits: one XOR and one wide multiply-add per chunk
             const char *gb = gbase + off;
             const uint32_t b32 = (uint32_t)base, va32 = (uint32_t)va, vb32 = (uint32_t)vb;
